@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark: converged projections/s on the Burgers-type 1-D projection workload.
+
+Workload (synthetic, seeded; the paper's trained flow models and PDE datasets are not
+available): family B (IC + per-slice mass + energy + boundary invariant), B = 512 samples,
+nx = 128, nt = 100, FP64.  A step is one snap_project call over one batch of 512 samples
+(parameter derivation, the moment-path Newton-KKT kernel, per-sample statistics).  Four
+distinct input/output sets rotate between steps so the working set (4 x 107 MB) exceeds the
+126 MB L2.  A sample counts as converged when its status is OK and ||h||_inf <= 1e-8 over all
+nominal rows, recomputed after the timed region from the written u (snap_constraint_residual).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank projects its own 512-sample shard (weak scaling, no collective on
+the data path); timing is the max over ranks.  --impl reference times the oracle (dense
+Newton-KKT on the host cores) on bounded samples of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "converged projections/s (‖h‖∞≤1e-8), 1D Burgers B=512; adjoint/forward time"
+UNIT = "projections/s"
+WORKLOAD = dict(name="burgers_1d", family="B", B=512, nx=128, nt=100, seed=1001)
+H_TOL = 1e-8
+ROTATE = 4
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_traffic(name, source):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
+    try:
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
+    if rec.get("source_sha256") != h:
+        return None
+    return rec.get("traffic_bytes_per_launch_full_size")
+
+
+# ---------------------------------------------------------------------------------------
+# oracle timing (cpu baseline / reference arm)
+# ---------------------------------------------------------------------------------------
+def oracle_rate(uh, pr, budget_s=10.0, chunk=8, nthreads=0):
+    """Run the oracle on chunks of samples until budget_s elapses; converged samples / s."""
+    from oracle import solve
+    w = WORKLOAD
+    t0 = time.perf_counter()
+    done = conv = 0
+    while done < uh.shape[0]:
+        sl = slice(done, min(done + chunk, uh.shape[0]))
+        _, _, st, _, _ = solve.project_1d(w["family"], w["nx"], w["nt"], pr[sl], uh[sl], nthreads=nthreads)
+        conv += int(((st["status"] == 0) & (st["h_inf"] <= H_TOL)).sum())
+        done = sl.stop
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    el = time.perf_counter() - t0
+    return conv / el, done, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from oracle import solve
+    from paper_2607_00095_b300 import synthetic
+    w = WORKLOAD
+    uh, pr = synthetic.gen_1d(w["seed"], w["B"], w["nx"], w["nt"], w["family"])
+    chunk = 8
+    nthreads = solve.max_threads()
+    for s in range(args.warmup):
+        i = (s * chunk) % w["B"]
+        solve.project_1d(w["family"], w["nx"], w["nt"], pr[i:i + chunk], uh[i:i + chunk])
+    conv = 0
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        i = ((args.warmup + s) * chunk) % w["B"]
+        _, _, st, _, _ = solve.project_1d(w["family"], w["nx"], w["nt"], pr[i:i + chunk], uh[i:i + chunk])
+        conv += int(((st["status"] == 0) & (st["h_inf"] <= H_TOL)).sum())
+    el = time.perf_counter() - t0
+    value = conv / el
+    sample = f"{chunk} samples of the {w['name']} workload per step (rotating through the 512), dense Newton-KKT"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": w["name"], "family": w["family"], "B": w["B"], "nx": w["nx"],
+                       "nt": w["nt"], "samples_per_step": chunk},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2607_00095_b300 import Problem, api, decode_stats, options, synthetic
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    w = WORKLOAD
+    B, nx, nt = w["B"], w["nx"], w["nt"]
+    p = Problem(w["family"], nx, nt)
+    opts = options()
+
+    # rotating input / output sets (different seeds per set and per rank)
+    sets = []
+    host0 = None
+    for r in range(ROTATE):
+        seed = w["seed"] + 7919 * r + 104729 * rank
+        uh, pr = synthetic.gen_1d(seed, B, nx, nt, w["family"])
+        if r == 0:
+            host0 = (uh, pr)
+        d_uh = torch.as_tensor(uh.reshape(B, -1), device=dev)
+        d_pr = torch.as_tensor(pr, device=dev)
+        out = (torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        sets.append((d_uh, d_pr, out))
+    ws = p.workspace(B, dev)
+
+    def step(i):
+        d_uh, d_pr, out = sets[i % ROTATE]
+        p.project(d_uh, d_pr, opts=opts, out=out, workspace=ws)
+        return api.last_launch_count()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    api.profile_reset()
+    api.profile_enable(True)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record()
+    for i in range(args.steps):
+        launches += step(i)
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    api.profile_enable(False)
+    clk = clocks.stop()
+    elapsed_ms = e0.elapsed_time(e1)
+    k_ms, k_n = api.profile_read("k1d_moment")
+    api.profile_reset()
+
+    # converged samples of each set, from the written u (untimed)
+    conv_per_set = []
+    for d_uh, d_pr, out in sets:
+        _, hinf = p.residual(out[0], d_pr, want_rows=False)
+        st = decode_stats(out[2])
+        ok = (st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)
+        conv_per_set.append(int(ok.sum()))
+    conv = sum(conv_per_set[i % ROTATE] for i in range(args.steps))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+        c = torch.tensor([conv], dtype=torch.float64, device=dev)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        conv = int(c.item())
+    value = conv / (elapsed_ms / 1e3)
+
+    # adjoint / forward time (differentiation workload: same shapes, dL/du ~ N(0, 1))
+    gbar = torch.as_tensor(synthetic.gen_gbar(1002, (B, nt * nx)), device=dev)
+    d_uh, d_pr, out = sets[0]
+    cache = torch.empty(p.cache_bytes(B), dtype=torch.uint8, device=dev)
+    reps = 20
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    u0, lam0, st0 = out
+    fwd_ms = timed(lambda: p.project(d_uh, d_pr, opts=opts, out=out, workspace=ws))
+    fwdc_ms = timed(lambda: lib_project_cache(p, d_uh, d_pr, opts, out, cache, ws))
+    bwd_c_ms = timed(lambda: p.backward(gbar, u0, lam0, d_pr, stats=st0, cache=cache))
+    bwd_r_ms = timed(lambda: p.backward(gbar, u0, lam0, d_pr, stats=st0, cache=None))
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        uh_h = torch.as_tensor(host0[0].reshape(B, -1)).pin_memory()
+        pr_h = torch.as_tensor(host0[1]).pin_memory()
+        u_h = torch.empty_like(uh_h).pin_memory()
+        st_h = torch.empty(B, 40, dtype=torch.uint8).pin_memory()
+        d_uh2 = torch.empty_like(d_uh)
+        d_pr2 = torch.empty_like(d_pr)
+        out2 = (torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+                torch.empty(B, 40, dtype=torch.uint8, device=dev))
+
+        def e2e_step():
+            d_uh2.copy_(uh_h, non_blocking=True)
+            d_pr2.copy_(pr_h, non_blocking=True)
+            p.project(d_uh2, d_pr2, opts=opts, out=out2, workspace=ws)
+            u_h.copy_(out2[0], non_blocking=True)
+            st_h.copy_(out2[2], non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        n_e2e = max(5, min(args.steps, 20))
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(n_e2e):
+            e2e_step()
+        b.record()
+        torch.cuda.synchronize()
+        e2e_ms = a.elapsed_time(b) / n_e2e
+        st = np.frombuffer(st_h.numpy().tobytes(), dtype=api.STATS_DTYPE)
+        conv_e2e = int(((st["status"] == 0) & (st["h_inf"] <= H_TOL)).sum())
+        e2e = {"value": conv_e2e * world / (e2e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(uh_h.numel() * 8 + pr_h.numel() * 8),
+               "d2h_bytes_per_step": int(u_h.numel() * 8 + st_h.numel()),
+               "ms_per_step": e2e_ms}
+
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm else "fallback"
+    hbm = hbm or 6400.0
+    bytes_per_sample = 8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40
+    launch_bytes = bytes_per_sample * B
+    k_avg_ms = k_ms / max(k_n, 1)
+    achieved = launch_bytes / (k_avg_ms / 1e3) / 1e9
+    traffic = kernel_traffic("k1d_moment", "paper_2607_00095_b300/csrc/kern_1d.cu")
+    fp64 = api.measure_fp64_rate(local)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import solve
+        rate, n_s, el = oracle_rate(*host0, budget_s=10.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": solve.max_threads(), "kind": "oracle",
+               "sample": f"first {n_s} samples of the {w['name']} workload (seed {w['seed']}), "
+                         f"dense Newton-KKT per connected component, {el:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "family": "B (IC, mass, energy, boundary invariant)",
+                       "B_per_gpu": B, "nx": nx, "nt": nt, "path": "moment",
+                       "l2": f"{ROTATE} rotating input/output sets of {launch_bytes / 1e6:.0f} MB (> 126 MB L2)"},
+            "converged_per_step": conv / args.steps,
+            "adjoint_forward_ratio": bwd_c_ms / fwdc_ms,
+            "adjoint": {"forward_ms": fwd_ms, "forward_store_ms": fwdc_ms, "backward_cached_ms": bwd_c_ms,
+                        "backward_recompute_ms": bwd_r_ms, "ratio_recompute": bwd_r_ms / fwd_ms,
+                        "cache_bytes": p.cache_bytes(B), "workspace_bytes": p.workspace_bytes(B)},
+            "roofline": {"bound": "hbm", "kernel": "k1d_moment", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                         "algorithmic_bytes_per_launch": launch_bytes, "kernel_ms": k_avg_ms,
+                         "peak_source": peak_src},
+            "fp64_fma_per_s": fp64,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def lib_project_cache(p, d_uh, d_pr, opts, out, cache, ws):
+    """Forward call that also writes the adjoint cache (the differentiation workload)."""
+    import ctypes as C
+
+    from paper_2607_00095_b300 import api
+    u, lam, st = out
+    api.check(api.lib().snap_project(p.handle, d_uh.shape[0], api._ptr(d_uh), api._ptr(d_pr), None,
+                                     api._ptr(u), api._ptr(lam), api._ptr(st), api._ptr(cache),
+                                     C.byref(opts), api._ptr(ws), ws.numel(), api._stream()))
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

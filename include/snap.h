@@ -1,0 +1,301 @@
+/*
+ * snap.h -- C ABI of the B300 batched nonlinear constraint projection library (libsnap.so).
+ *
+ * The library computes, for every sample b of a batch, the projection of eq. (2) of the
+ * paper (Sampling section; restated in "Jacobian Structure"):
+ *
+ *     u_b = argmin_u 1/2 || u - u_hat_b ||^2   subject to  h(u; theta_b) = 0,
+ *
+ * by Newton iterations on the KKT conditions of Appendix B ("newtonKKTsystem"):
+ *
+ *     [ W  J^T ] [du  ]     [ u - u_hat + J^T lambda ]
+ *     [ J  0   ] [dlam] = - [ h(u)                   ],  W = I + sum_r lambda_r Hess h_r,
+ *
+ * with L = f + lambda^T h.  The Jacobian of h has a fixed block-sparse pattern: blocks are
+ * independent across samples ("Jacobian Structure": block-diagonal over the batch) and,
+ * for the families here, across time slices / frames too.
+ *
+ * Conventions for every entry point:
+ *   - All numeric arrays are IEEE FP64, C order, and live in DEVICE memory unless the
+ *     argument says "host".  The caller allocates and owns every buffer; the library
+ *     never allocates inside snap_project / snap_project_backward / snap_constraint_residual
+ *     / snap_batch_project, so those calls can be enqueued on a stream and captured into
+ *     a CUDA graph.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *     that take a stream are asynchronous with respect to the host; results are ready
+ *     when the stream reaches that point.
+ *   - Errors in arguments are reported by the return code and a thread-local message
+ *     (snap_last_error).  Per-sample numerical outcomes (non-convergence, non-finite
+ *     input, ...) are NOT call errors: they are written to snap_stats.status.
+ *   - Device code never traps and never waits on other blocks.
+ *
+ * Layouts (x fastest, the flattening of Appendix C):
+ *   1-D families A/B:  u[b][k][i], k < nt time slices, i < nx points, x_i = i/nx periodic,
+ *                      t_k = k/(nt-1).
+ *   2-D family C:      w[b][f][c][j][i], f < nt frames, c = 0 (u) / 1 (v), j = y, i = x,
+ *                      N x N periodic grid, dx = 1/N, t_f = f/(nt-1).
+ *   Multipliers lambda[b][r] in the nominal row order (rows implied by other rows are
+ *   listed but carry lambda = 0):
+ *     A/B: IC rows (nx) | mass rows (nt) | energy rows (nt) | boundary rows (nt, family B)
+ *          (only the row types enabled in snap_problem_desc.rows, in this order)
+ *     C:   divergence rows [f][j][i] (nt*N*N) | kinetic-energy rows (nt)
+ *   Parameters params[b][*]:
+ *     A/B: g[0..nx-1] (IC values), r (energy decay rate), c[0..nt-1] (family B only)
+ *     C:   K0, r2  (kinetic energy K_f = K0 exp(-r2 t_f))
+ */
+#ifndef SNAP_H
+#define SNAP_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define SNAP_API __attribute__((visibility("default")))
+#else
+#define SNAP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct snap_problem *snap_problem_t;
+typedef struct snap_batch *snap_batch_t;
+typedef void *snap_stream_t; /* cudaStream_t */
+
+typedef enum {
+  SNAP_OK = 0,
+  SNAP_ERR_INVALID_ARG = 1,  /* bad descriptor, null pointer, size out of range */
+  SNAP_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+  SNAP_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has the CUDA error) */
+  SNAP_ERR_NO_MEMORY = 4,    /* host or device allocation failed in a create call */
+  SNAP_ERR_WORKSPACE = 5,    /* workspace pointer missing or smaller than required */
+  SNAP_ERR_NOT_READY = 6     /* object used before it was completed (e.g. unbound batch) */
+} snap_status;
+
+/* Constraint families (Table I constraint types; Appendix A/C/D discretisations). */
+typedef enum {
+  /* 1-D space-time field: IC u(x_i,0) = g_i; per-slice mass dx sum_i u_{k,i} = M,
+   * M = dx sum g; per-slice energy dx sum_i u_{k,i}^2 = E_k,
+   * E_k = max(E0 exp(-r t_k), M^2 + energy_floor), E0 = dx sum g^2. */
+  SNAP_FAMILY_A_MASS_ENERGY = 0,
+  /* A plus the two-sided boundary invariant u_{k,0}^2 + u_{k,nx/2}^2 = c_k. */
+  SNAP_FAMILY_B_BURGERS_BOUNDARY = 1,
+  /* 2-D velocity per frame: central-difference divergence
+   * (u_{i+1,j} - u_{i-1,j} + v_{i,j+1} - v_{i,j-1}) / (2 dx) = 0 and kinetic energy
+   * 1/2 dx^2 sum(u^2 + v^2) = K0 exp(-r2 t_f). */
+  SNAP_FAMILY_C_DIV_ENERGY = 2,
+  /* Appendix C worked example (IC + left-Riemann mass differences).  Pattern queries
+   * only; snap_project returns SNAP_ERR_UNSUPPORTED for it. */
+  SNAP_FAMILY_TOY_LEFT_RIEMANN = 3
+} snap_family;
+
+/* Row-type bits for snap_problem_desc.rows (1-D families). */
+enum {
+  SNAP_ROW_IC = 1,
+  SNAP_ROW_MASS = 2,
+  SNAP_ROW_ENERGY = 4,
+  SNAP_ROW_BOUNDARY = 8
+};
+
+/* Per-sample outcome codes (snap_stats.status). */
+enum {
+  SNAP_SAMPLE_OK = 0,                /* ||F||_inf <= tol_kkt and ||h||_inf <= tol_h */
+  SNAP_SAMPLE_MAXITER = 1,           /* max_iter Newton steps without convergence */
+  SNAP_SAMPLE_LINESEARCH = 2,        /* no Armijo step within max_backtracks halvings */
+  SNAP_SAMPLE_NONFINITE = 3,         /* NaN/Inf met in the input or the iteration */
+  SNAP_SAMPLE_INFEASIBLE_PARAMS = 4, /* parameters admit no feasible point (c_k < 0) */
+  SNAP_SAMPLE_RESIDUAL = 5,          /* KKT converged but some nominal row (one left out of
+                                        the solve) has |h| > tol_h: inconsistent params */
+  SNAP_SAMPLE_SINGULAR = 6,          /* singular Newton-KKT matrix */
+  SNAP_SAMPLE_NOT_MINIMUM = 7        /* converged to a KKT point whose KKT matrix has the
+                                        wrong inertia (second-order condition fails) */
+};
+
+/* Solver paths for snap_options.path. */
+enum {
+  SNAP_PATH_AUTO = 0,     /* fastest path valid for the call */
+  SNAP_PATH_GENERAL = 1,  /* per-element FP64 Newton-KKT (any u0) */
+  SNAP_PATH_MOMENT = 2    /* moment-reduced Newton-KKT, FP64 scalars (u0 = u_hat only) */
+};
+
+typedef struct {
+  int family;          /* snap_family */
+  int nx;              /* 1-D: points per slice (even, 4..512); 2-D: N (even, >= 4) */
+  int ny;              /* 2-D: must equal nx; 1-D: ignored */
+  int nt;              /* 1-D: time slices; 2-D: frames (>= 2) */
+  unsigned rows;       /* 1-D: SNAP_ROW_* mask (IC required); 0 = family default */
+  double energy_floor; /* 1-D: floor in E_k (the workloads use 0.05) */
+  int max_batch;       /* 0, or an upper bound on B checked by every call */
+} snap_problem_desc;
+
+typedef struct {
+  int n_vars;              /* unknowns per sample */
+  int n_rows_nominal;      /* rows per sample, including implied rows (lambda length) */
+  int n_rows_active;       /* rows in the Newton-KKT system per sample */
+  int n_params;            /* parameters per sample */
+  long long pattern_nnz;   /* nonzeros of the Jacobian pattern over the nominal rows */
+  int n_blocks;            /* independent blocks per sample (1-D: nt, 2-D: nt frames) */
+} snap_info;
+
+typedef struct {
+  int iters;        /* Newton steps taken (max over the sample's blocks) */
+  int backtracks;   /* line-search halvings (sum over blocks) */
+  int status;       /* SNAP_SAMPLE_* (worst over blocks) */
+  int corrections;  /* inertia corrections (sum over blocks) */
+  double h_inf;     /* ||h(u)||_inf over ALL nominal rows at the returned u */
+  double kkt_inf;   /* ||F||_inf over the active system at the returned (u, lambda) */
+  double obj;       /* 1/2 ||u - u_hat||^2 */
+} snap_stats;
+
+typedef struct {
+  double tol_kkt;      /* stop when ||F||_inf <= tol_kkt (default 1e-10) */
+  double tol_h;        /* SNAP_SAMPLE_RESIDUAL threshold on ||h||_inf (default 1e-8) */
+  int max_iter;        /* default 50 (at most 10000) */
+  int max_backtracks;  /* default 30 (at most 200) */
+  double armijo_c1;    /* accept t when phi(t) <= (1 - 2 c1 t) phi(0); default 1e-4 */
+  double delta0;       /* first inertia-correction shift W + delta I (default 1e-8) */
+  int max_corrections; /* 0 (default): plain Newton-Raphson on F = 0; 1..100: shift W until
+                          the inertia of K is (n, m, 0), delta x10 each time */
+  int path;            /* SNAP_PATH_* (default AUTO) */
+  double w_keep;       /* each step keeps every diagonal entry of W at >= w_keep times its
+                          current value (default 0.01; 0 disables) */
+} snap_options;
+
+/* Message of the last failed call on this host thread ("" if none).  Never NULL. */
+SNAP_API const char *snap_last_error(void);
+
+/* Library version string. */
+SNAP_API const char *snap_version(void);
+
+/* Fill *opt with the defaults listed in snap_options.  Returns SNAP_ERR_INVALID_ARG if
+ * opt is NULL. */
+SNAP_API snap_status snap_options_default(snap_options *opt);
+
+/* Build a problem: validates the descriptor, fixes the row list and the Jacobian
+ * sparsity pattern over the nominal rows ("Jacobian Structure": the pattern does not change
+ * across iterations), marks the rows implied by others (left out of the solve), and builds
+ * the symbolic structure once (1-D: per-slice 3x3 Schur blocks; 2-D: the constant
+ * divergence Schur factor, see snap_problem_info).  Host call; allocates device memory for
+ * shared constant data.  *out is set only on success.  Errors: INVALID_ARG (bad sizes,
+ * ny != nx for C, IC bit missing, boundary bit for family A), NO_MEMORY, CUDA. */
+SNAP_API snap_status snap_problem_create(const snap_problem_desc *desc, snap_problem_t *out);
+
+/* Release a problem (NULL is a no-op).  Must not be in use by queued work. */
+SNAP_API void snap_problem_destroy(snap_problem_t p);
+
+/* Sizes of a problem.  Host call. */
+SNAP_API snap_status snap_problem_info(snap_problem_t p, snap_info *info);
+
+/* Sparsity pattern of the Jacobian over the nominal rows, CSR, HOST arrays:
+ * row_ptr[n_rows_nominal + 1], col_idx[pattern_nnz] (columns ascending in a row).
+ * Defined for every family (including the Appendix C toy family). */
+SNAP_API snap_status snap_problem_pattern(snap_problem_t p, int *row_ptr, int *col_idx);
+
+/* Which nominal rows take part in the solve (host array active[n_rows_nominal], 1/0). */
+SNAP_API snap_status snap_problem_active_rows(snap_problem_t p, unsigned char *active);
+
+/* Workspace bytes a call with batch size B needs (snap_project, snap_project_backward and
+ * snap_constraint_residual share one requirement). */
+SNAP_API snap_status snap_workspace_size(snap_problem_t p, int B, size_t *bytes);
+
+/* Bytes of the optional adjoint cache written by snap_project (per-block factor data). */
+SNAP_API snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes);
+
+/* Forward projection of B samples (eq. (2) solved by the Newton-KKT iteration of
+ * Appendix B with an Armijo line search on phi = 1/2 ||F||^2 and per-block convergence
+ * masks).
+ *   u_hat   [B][n_vars]    targets (device, read)
+ *   params  [B][n_params]  per-sample constraint parameters (device, read)
+ *   u0      [B][n_vars]    starting point, or NULL for u0 = u_hat (device, read)
+ *   u       [B][n_vars]    projected samples (device, written; may not alias inputs)
+ *   lambda  [B][n_rows_nominal] multipliers, sign of L = f + lambda^T h (device, written)
+ *   stats   [B]            per-sample statistics (device, written) or NULL
+ *   adjoint_cache          NULL, or snap_adjoint_cache_size bytes (device, written) that
+ *                          snap_project_backward can reuse instead of refactoring
+ *   opt                    NULL for defaults (host)
+ *   workspace              snap_workspace_size(p, B) bytes of device scratch
+ * Errors: INVALID_ARG (B < 0, B > max_batch, null required pointer, bad options),
+ * WORKSPACE, UNSUPPORTED (toy family; MOMENT path with u0 != NULL), CUDA (launch failed).
+ * B = 0 is a no-op. */
+SNAP_API snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const double *params,
+                         const double *u0, double *u, double *lambda, snap_stats *stats,
+                         void *adjoint_cache, const snap_options *opt, void *workspace,
+                         size_t workspace_bytes, snap_stream_t stream);
+
+/* Backward pass of the projection by the implicit-function theorem on
+ * F(u, lambda; u_hat, theta) = 0 (Appendix B system at the solution, no inertia shift):
+ *     K [a ; b] = [grad_u ; 0],  dL/du_hat = a,  dL/dtheta = -b^T dh/dtheta.
+ *   grad_u      [B][n_vars]    upstream gradient dL/du (device, read)
+ *   u, lambda   forward outputs (device, read)
+ *   params      forward parameters (device, read)
+ *   stats       forward stats (device) or NULL; samples whose status is not OK get NaN
+ *   adjoint_cache  the cache snap_project wrote, or NULL to recompute the factors from u
+ *   grad_u_hat  [B][n_vars]    (device, written)
+ *   grad_params [B][n_params]  (device, written) or NULL; layout of params
+ *   workspace   snap_workspace_size(p, B) bytes
+ * Errors as snap_project. */
+SNAP_API snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
+                                  const double *u, const double *lambda, const double *params,
+                                  const snap_stats *stats, const void *adjoint_cache,
+                                  double *grad_u_hat, double *grad_params, void *workspace,
+                                  size_t workspace_bytes, snap_stream_t stream);
+
+/* Constraint residual h(u; theta) of every nominal row (the per-type constraint error of
+ * the Additional Results section is computed from it).
+ *   h      [B][n_rows_nominal] (device, written) or NULL
+ *   h_inf  [B] max_r |h_r| (device, written) or NULL */
+SNAP_API snap_status snap_constraint_residual(snap_problem_t p, int B, const double *u,
+                                     const double *params, double *h, double *h_inf,
+                                     void *workspace, size_t workspace_bytes,
+                                     snap_stream_t stream);
+
+/* ---------------- uneven batches in one persistent launch ---------------- */
+
+/* A batch of n_inst instances; instance i is one sample of problem probs[inst_problem[i]]
+ * (host arrays).  The problems must outlive the batch.  All instance sizes may differ. */
+SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *probs, int n_inst,
+                              const int *inst_problem, snap_batch_t *out);
+SNAP_API void snap_batch_destroy(snap_batch_t b);
+
+/* Bind the device buffers of every instance (host arrays of device pointers, length
+ * n_inst).  Copies the pointer table to the device synchronously; call again to rebind.
+ * lambda and stats rows are per instance. */
+SNAP_API snap_status snap_batch_bind(snap_batch_t b, const double *const *u_hat,
+                            const double *const *params, double *const *u,
+                            double *const *lambda, snap_stats *stats);
+
+/* Workspace for snap_batch_project. */
+SNAP_API snap_status snap_batch_workspace_size(snap_batch_t b, size_t *bytes);
+
+/* Project every bound instance in ONE persistent kernel launch: blocks pull work items
+ * (instance, block range) from a queue in the workspace.  t_ns (device, [n_inst][2]) or
+ * NULL receives each instance's first-start and last-end %globaltimer stamps. */
+SNAP_API snap_status snap_batch_project(snap_batch_t b, const snap_options *opt, unsigned long long *t_ns,
+                               void *workspace, size_t workspace_bytes, snap_stream_t stream);
+
+/* Same work as snap_batch_project but one plain launch per (family, size) group. */
+SNAP_API snap_status snap_batch_project_grouped(snap_batch_t b, const snap_options *opt, void *workspace,
+                                       size_t workspace_bytes, snap_stream_t stream);
+
+/* ---------------- measurement helpers ---------------- */
+
+/* Measured FP64 FMA rate of device `device` (FMAs per second) from a short in-register
+ * kernel; used to state the arithmetic roofline.  Host call, synchronous. */
+SNAP_API snap_status snap_measure_fp64_rate(int device, double *fma_per_s);
+
+/* Per-kernel timing: when enabled, every kernel launch of the library outside stream capture
+ * is bracketed by two CUDA events recorded on its stream.  snap_profile_read waits for the
+ * recorded events of kernel `name` (e.g. "k1d_moment") and returns their summed elapsed time
+ * and count; snap_profile_reset drops all records.  Host calls. */
+SNAP_API snap_status snap_profile_enable(int on);
+SNAP_API snap_status snap_profile_reset(void);
+SNAP_API snap_status snap_profile_read(const char *name, double *total_ms, long long *launches);
+
+/* Number of kernels launched by the last snap_* call on this host thread. */
+SNAP_API int snap_last_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SNAP_H */

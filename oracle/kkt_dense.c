@@ -26,10 +26,16 @@
  *     J_rj = A_rj + 2 Q_rj u_j,     W = I + sum_r lam_r * 2 diag(Q_r).
  *
  * Globalisation (the paper is silent; these are the readings written down in the design doc):
- *   start u = u0 (default u_hat), lam = 0; stop when ||F||_inf <= tol_kkt; merit
- *   phi = 1/2 ||F||_2^2 with Armijo backtracking (t = 1, halve until
- *   phi(t) <= (1 - 2 c1 t) phi(0), at most max_backtracks halvings); inertia correction
- *   W <- W + delta I (delta = delta0, then x10) whenever the inertia of K is not (n, m, 0).
+ *   Newton-Raphson on F(u, lam) = 0 exactly as Appendix B derives it, from u = u0 (default
+ *   u_hat), lam = 0; stop when ||F||_inf <= tol_kkt; merit phi = 1/2 ||F||_2^2, for which
+ *   the Newton step is a descent direction whenever K is nonsingular; Armijo backtracking
+ *   (halve t until phi(t) <= (1 - 2 c1 t) phi(0), at most max_backtracks halvings) from
+ *   the largest t <= 1 that keeps every diagonal entry of W at >= w_keep times its current
+ *   value (W is diagonal and linear in lam for these constraint forms; this keeps W positive
+ *   definite, hence K of inertia (n, m, 0) when J has full row rank, and makes a limit
+ *   point a strict local minimum).  At a converged point the inertia of K is checked
+ *   (second-order sufficient condition); failure gives status NOT_MINIMUM.
+ *   Optional (max_corrections > 0): Ipopt-style inertia correction W <- W + delta I.
  *
  * Separability.  The objective is a sum over variables and each constraint touches a
  * subset of them, so the projection splits exactly into independent problems, one per
@@ -52,7 +58,8 @@
 #include <omp.h>
 #endif
 
-enum { ORA_OK = 0, ORA_MAXITER = 1, ORA_LINESEARCH = 2, ORA_NONFINITE = 3, ORA_SINGULAR = 6 };
+enum { ORA_OK = 0, ORA_MAXITER = 1, ORA_LINESEARCH = 2, ORA_NONFINITE = 3, ORA_SINGULAR = 6,
+       ORA_NOT_MINIMUM = 7 };
 
 typedef struct {
   double tol_kkt;
@@ -62,6 +69,7 @@ typedef struct {
   double delta0;
   int max_corrections;
   int split_components;
+  double w_keep;
 } ora_opts;
 
 typedef struct {
@@ -433,7 +441,9 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
     if (!isfinite(res)) { st->status = ORA_NONFINITE; break; }
     if (res <= o->tol_kkt) { st->status = ORA_OK; break; }
     if (it >= o->max_iter) { st->status = ORA_MAXITER; break; }
-    /* Newton-KKT system with inertia correction */
+    /* Newton-KKT system.  max_corrections = 0: plain Newton-Raphson on F = 0 (Appendix B);
+     * its step is a descent direction of phi whenever K is nonsingular.  max_corrections > 0:
+     * additionally shift W <- W + delta I until the inertia is (n, m, 0). */
     double delta = 0.0;
     int ok = 0;
     for (int corr = 0; corr <= o->max_corrections; ++corr) {
@@ -441,15 +451,33 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
       double kmax = 0.0;
       for (int i = 0; i < N * N; ++i) if (fabs(K[i]) > kmax) kmax = fabs(K[i]);
       ldl_factor(K, &f, (double)N * 2.220446049250313e-16 * (kmax > 0 ? kmax : 1.0));
-      if (f.n_pos == nv && f.n_neg == c->mr && f.n_zero == 0) { ok = 1; break; }
+      if (f.n_zero == 0 && (o->max_corrections == 0 || (f.n_pos == nv && f.n_neg == c->mr))) {
+        ok = 1;
+        break;
+      }
       delta = (delta == 0.0) ? o->delta0 : delta * 10.0;
       st->corrections++;
     }
     if (!ok) { st->status = ORA_SINGULAR; break; }
     for (int i = 0; i < N; ++i) Ft[i] = -F[i];
     if (ldl_solve(&f, Ft, dz) != 0) { st->status = ORA_SINGULAR; break; }
-    /* Armijo backtracking on phi = 1/2 ||F||^2 */
+    /* Largest first trial t <= 1 that keeps every diagonal entry of W = I + sum_r lam_r
+     * 2 diag(Q_r) (linear in lam) at >= w_keep times its current value, when the current W
+     * is positive definite: fraction to the boundary of {lam : W(lam) > 0}. */
     double t = 1.0;
+    if (o->w_keep > 0.0) {
+      for (int j = 0; j < nv; ++j) {
+        double w = 1.0, dw = 0.0;
+        for (int k = 0; k < c->mr; ++k)
+          for (int p = c->qp[k]; p < c->qp[k + 1]; ++p)
+            if (c->qc[p] == j) { w += 2.0 * c->qv[p] * lam[k]; dw += 2.0 * c->qv[p] * dz[nv + k]; }
+        if (w > 0.0 && dw < 0.0) {
+          double tm = (1.0 - o->w_keep) * w / (-dw);
+          if (tm < t) t = tm;
+        }
+      }
+    }
+    /* Armijo backtracking on phi = 1/2 ||F||^2 */
     int nb = 0, accepted = 0;
     double phit = phi;
     for (;;) {
@@ -470,6 +498,15 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
     phi = phit;
     res = norm_inf(F, N);
     st->iters = it + 1;
+  }
+  /* second-order sufficient condition at a converged point: K has inertia (n, m, 0) iff W
+   * is positive definite on null(J) (J of full row rank) */
+  if (st->status == ORA_OK && c->mr + nv > 0) {
+    build_K(c, u, lam, 0.0, K);
+    double kmax = 0.0;
+    for (int i = 0; i < N * N; ++i) if (fabs(K[i]) > kmax) kmax = fabs(K[i]);
+    ldl_factor(K, &f, (double)N * 2.220446049250313e-16 * (kmax > 0 ? kmax : 1.0));
+    if (!(f.n_pos == nv && f.n_neg == c->mr && f.n_zero == 0)) st->status = ORA_NOT_MINIMUM;
   }
   st->kkt_inf = res;
   st->phi = phi;
@@ -504,9 +541,10 @@ static int status_rank(int s) {  /* worse status wins when aggregating a sample 
     case ORA_OK: return 0;
     case ORA_MAXITER: return 1;
     case ORA_LINESEARCH: return 2;
-    case ORA_SINGULAR: return 3;
-    case ORA_NONFINITE: return 4;
-    default: return 5;
+    case ORA_NOT_MINIMUM: return 3;
+    case ORA_SINGULAR: return 4;
+    case ORA_NONFINITE: return 5;
+    default: return 6;
   }
 }
 

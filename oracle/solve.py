@@ -10,13 +10,13 @@ import numpy as np
 from . import build as _build
 from . import problems
 
-ORA_OK, ORA_MAXITER, ORA_LINESEARCH, ORA_NONFINITE, ORA_SINGULAR = 0, 1, 2, 3, 6
+ORA_OK, ORA_MAXITER, ORA_LINESEARCH, ORA_NONFINITE, ORA_SINGULAR, ORA_NOT_MINIMUM = 0, 1, 2, 3, 6, 7
 
 
 class OraOpts(C.Structure):
     _fields_ = [("tol_kkt", C.c_double), ("max_iter", C.c_int), ("max_backtracks", C.c_int),
                 ("c1", C.c_double), ("delta0", C.c_double), ("max_corrections", C.c_int),
-                ("split_components", C.c_int)]
+                ("split_components", C.c_int), ("w_keep", C.c_double)]
 
 
 class OraStats(C.Structure):
@@ -50,7 +50,7 @@ def _p(a, ct):
 
 def default_opts(**kw):
     o = dict(tol_kkt=1e-10, max_iter=50, max_backtracks=30, c1=1e-4, delta0=1e-8,
-             max_corrections=40, split_components=1)
+             max_corrections=0, split_components=1, w_keep=0.01)
     o.update(kw)
     return OraOpts(**o)
 

@@ -1,0 +1,255 @@
+// Newton-KKT for one 1-D time slice (k >= 1) of families A/B in moment form.
+//
+// Rows of slice k (Appendix B notation, L = f + lambda^T h, f = 1/2 ||u - u_hat||^2):
+//   mass     h_m = dx sum_i u_i - M
+//   energy   h_e = dx sum_i u_i^2 - E
+//   boundary h_b = u_0^2 + u_h^2 - C          (h = nx/2)
+// grad_u L = u - u_hat + dx lam_m 1 + 2 dx lam_e u + 2 lam_b (u_0 e_0 + u_h e_h)
+// W = diag(alpha on the interior, beta at i in {0, h}), alpha = 1 + 2 dx lam_e,
+// beta = alpha + 2 lam_b.
+//
+// Moment form.  W is uniform on the interior (i not in {0, h}) and grad_u L_i is affine in
+// (u_i, u_hat_i) with coefficients shared by the interior, so a Newton step maps an interior
+// iterate of the form u_i = a u_hat_i + c to another one of the same form.  Starting from
+// u = u_hat (a = 1, c = 0), every iterate, line-search trial and the solution are therefore
+// described by (a, c, u_0, u_h, lam_m, lam_e, lam_b), and every sum the Newton-KKT step
+// needs reduces to the interior moments S1 = sum u_hat_i, S2 = sum u_hat_i^2 (and the
+// interior max / min of u_hat for the infinity norm of F).  The iteration below is the
+// same sequence of Newton-KKT steps, line-search trials and stopping tests as the dense
+// per-element iteration, evaluated in O(1) per step.
+//
+// Newton step through the Schur complement of the KKT matrix of Appendix B:
+//   S dlam = h - J W^-1 grad L,  S = J W^-1 J^T (3x3),  du = -W^-1 (grad L + J^T dlam).
+// Inertia of K = In(W) + In(-S) (Haynsworth); the required inertia is (nx, m, 0).
+// Globalisation: Armijo on phi = 1/2 ||F||^2, first trial capped so that W stays positive
+// definite (both of its diagonal values keep >= w_keep of their current value); the
+// second-order condition is checked at the converged point.
+#pragma once
+
+#include "snap_internal.h"
+
+template <class T>
+struct SliceIn {
+  T S1, S2, mx, mn;   // interior moments / extremes of u_hat
+  T uh0, uhh;         // u_hat at i = 0 and i = nx/2
+  T n;                // interior count nx - 2
+  T dx, M, E, C;      // rhs of the slice rows
+  int rows;           // SL_* bits
+};
+
+template <class T>
+struct SliceZ {
+  T a, c, p0, ph, lm, le, lb;
+};
+
+template <class T>
+struct SliceEval {
+  T alpha, beta, P, Q, su, su2, g0, gh, hm, he, hb, phi, res;
+};
+
+template <class T>
+__device__ __forceinline__ T sl_abs(T x) { return x < T(0) ? -x : x; }
+
+template <class T>
+__device__ __forceinline__ T sl_max(T x, T y) { return (x < y) ? y : x; }
+
+// phi and ||F||_inf at z; NaN propagates into res through the comparisons below
+template <class T>
+__device__ __forceinline__ void slice_eval(const SliceIn<T> &d, const SliceZ<T> &z,
+                                           SliceEval<T> &e) {
+  const T two = T(2), one = T(1);
+  e.alpha = one + two * d.dx * z.le;
+  e.beta = e.alpha + two * z.lb;
+  e.P = e.alpha * z.a - one;
+  e.Q = e.alpha * z.c + d.dx * z.lm;
+  e.su = z.a * d.S1 + z.c * d.n;
+  e.su2 = z.a * z.a * d.S2 + two * z.a * z.c * d.S1 + z.c * z.c * d.n;
+  e.g0 = e.beta * z.p0 - d.uh0 + d.dx * z.lm;
+  e.gh = e.beta * z.ph - d.uhh + d.dx * z.lm;
+  const T pp = z.p0 * z.p0 + z.ph * z.ph;
+  e.hm = (d.rows & SL_MASS) ? d.dx * (e.su + z.p0 + z.ph) - d.M : T(0);
+  e.he = (d.rows & SL_ENERGY) ? d.dx * (e.su2 + pp) - d.E : T(0);
+  e.hb = (d.rows & SL_BOUND) ? pp - d.C : T(0);
+  T gi2 = e.P * e.P * d.S2 + two * e.P * e.Q * d.S1 + e.Q * e.Q * d.n;
+  if (gi2 < T(0)) gi2 = T(0);
+  const T ginf = sl_max(sl_abs(e.P * d.mx + e.Q), sl_abs(e.P * d.mn + e.Q));
+  e.phi = T(0.5) * (gi2 + e.g0 * e.g0 + e.gh * e.gh + e.hm * e.hm + e.he * e.he + e.hb * e.hb);
+  T r = ginf;
+  T c;
+  c = sl_abs(e.g0); r = (r < c || c != c) ? c : r;
+  c = sl_abs(e.gh); r = (r < c || c != c) ? c : r;
+  c = sl_abs(e.hm); r = (r < c || c != c) ? c : r;
+  c = sl_abs(e.he); r = (r < c || c != c) ? c : r;
+  c = sl_abs(e.hb); r = (r < c || c != c) ? c : r;
+  if (e.phi != e.phi) r = e.phi;
+  e.res = r;
+}
+
+// 3x3 symmetric LDL^T without pivoting; returns false on a zero pivot.
+template <class T>
+struct Ldl3 {
+  T d0, d1, d2, l10, l20, l21;
+};
+
+template <class T>
+__device__ __forceinline__ bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T s22,
+                                            Ldl3<T> &f) {
+  f.d0 = s00;
+  if (f.d0 == T(0)) return false;
+  f.l10 = s01 / f.d0;
+  f.l20 = s02 / f.d0;
+  f.d1 = s11 - f.l10 * s01;
+  if (f.d1 == T(0)) return false;
+  f.l21 = (s12 - f.l20 * s01) / f.d1;
+  f.d2 = s22 - f.l20 * s02 - f.l21 * (s12 - f.l20 * s01);
+  if (f.d2 == T(0)) return false;
+  return true;
+}
+
+template <class T>
+__device__ __forceinline__ void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T &x0, T &x1,
+                                           T &x2) {
+  const T y0 = r0;
+  const T y1 = r1 - f.l10 * y0;
+  const T y2 = r2 - f.l20 * y0 - f.l21 * y1;
+  x2 = y2 / f.d2;
+  x1 = y1 / f.d1 - f.l21 * x2;
+  x0 = y0 / f.d0 - f.l10 * x1 - f.l20 * x2;
+}
+
+// Schur complement S = J W^-1 J^T of the slice rows at z with W diagonal (w interior, wb at
+// the two boundary points); absent rows get an identity row so their dlam is 0.
+template <class T>
+__device__ __forceinline__ void slice_schur(const SliceIn<T> &d, const SliceZ<T> &z, T su,
+                                            T su2, T w, T wb, T &s00, T &s01, T &s02, T &s11,
+                                            T &s12, T &s22) {
+  const T two = T(2), four = T(4);
+  const T iw = T(1) / w, iwb = T(1) / wb;
+  const T pp = z.p0 * z.p0 + z.ph * z.ph;
+  const T ps = z.p0 + z.ph;
+  const bool hm = d.rows & SL_MASS, he = d.rows & SL_ENERGY, hb = d.rows & SL_BOUND;
+  s00 = hm ? d.dx * d.dx * (d.n * iw + two * iwb) : T(1);
+  s01 = (hm && he) ? two * d.dx * d.dx * (su * iw + ps * iwb) : T(0);
+  s02 = (hm && hb) ? two * d.dx * ps * iwb : T(0);
+  s11 = he ? four * d.dx * d.dx * (su2 * iw + pp * iwb) : T(1);
+  s12 = (he && hb) ? four * d.dx * pp * iwb : T(0);
+  s22 = hb ? four * pp * iwb : T(1);
+}
+
+// Inertia test of K via In(W) + In(-S).  nint = interior count, m = rows present.
+template <class T>
+__device__ __forceinline__ bool slice_inertia_ok(const Ldl3<T> &f, T w, T wb, int nint,
+                                                 int m_present, int n_absent) {
+  if (w == T(0) || wb == T(0)) return false;
+  const int npW = (w > T(0) ? nint : 0) + (wb > T(0) ? 2 : 0);
+  const int nnW = (w < T(0) ? nint : 0) + (wb < T(0) ? 2 : 0);
+  int npS = (f.d0 > T(0)) + (f.d1 > T(0)) + (f.d2 > T(0)) - n_absent;
+  int nnS = (f.d0 < T(0)) + (f.d1 < T(0)) + (f.d2 < T(0));
+  return (npW + nnS == nint + 2) && (nnW + npS == m_present);
+}
+
+struct SliceResult {
+  int iters, backtracks, status, corrections;
+};
+
+// Run the Newton-KKT iteration of one slice.  z holds the start on entry and the last
+// accepted iterate on exit; e its evaluation.
+template <class T>
+__device__ inline SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
+                                           const SolverOpts &o) {
+  SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
+  const int m_present = ((d.rows & SL_MASS) != 0) + ((d.rows & SL_ENERGY) != 0) +
+                        ((d.rows & SL_BOUND) != 0);
+  const int n_absent = 3 - m_present;
+  const int nint = (int)d.n;  // only used for the inertia count
+  slice_eval(d, z, e);
+  for (int it = 0;; ++it) {
+    if (!(e.res == e.res) || isinf((double)e.res)) { R.status = SNAP_SAMPLE_NONFINITE; break; }
+    if (e.res <= T(o.tol_kkt)) { R.status = SNAP_SAMPLE_OK; break; }
+    if (it >= o.max_iter) { R.status = SNAP_SAMPLE_MAXITER; break; }
+    // Newton-KKT system.  max_corrections = 0: plain Newton-Raphson (Appendix B); > 0:
+    // shift W + delta I until the inertia of K is (nx, m, 0).
+    T delta = T(0);
+    Ldl3<T> f;
+    bool ok = false;
+    T w = e.alpha, wb = e.beta;
+    for (int corr = 0; corr <= o.max_corrections; ++corr) {
+      w = e.alpha + delta;
+      wb = e.beta + delta;
+      T s00, s01, s02, s11, s12, s22;
+      slice_schur(d, z, e.su, e.su2, w, wb, s00, s01, s02, s11, s12, s22);
+      if (w != T(0) && wb != T(0) && ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
+          (o.max_corrections == 0 || slice_inertia_ok(f, w, wb, nint, m_present, n_absent))) {
+        ok = true;
+        break;
+      }
+      delta = (delta == T(0)) ? T(o.delta0) : delta * T(10);
+      R.corrections++;
+    }
+    if (!ok) { R.status = SNAP_SAMPLE_SINGULAR; break; }
+    // rhs r = h - J W^-1 grad L
+    const T two = T(2);
+    const T iw = T(1) / w, iwb = T(1) / wb;
+    const T sg = e.P * d.S1 + e.Q * d.n;                                     // sum_int gL
+    const T sug = z.a * e.P * d.S2 + (z.a * e.Q + z.c * e.P) * d.S1 + z.c * e.Q * d.n;
+    const T pg = z.p0 * e.g0 + z.ph * e.gh;
+    T r0 = (d.rows & SL_MASS) ? e.hm - d.dx * (sg * iw + (e.g0 + e.gh) * iwb) : T(0);
+    T r1 = (d.rows & SL_ENERGY) ? e.he - two * d.dx * (sug * iw + pg * iwb) : T(0);
+    T r2 = (d.rows & SL_BOUND) ? e.hb - two * pg * iwb : T(0);
+    T dlm, dle, dlb;
+    ldl3_solve(f, r0, r1, r2, dlm, dle, dlb);
+    // du = -W^-1 (grad L + J^T dlam)
+    SliceZ<T> dz;
+    dz.lm = dlm; dz.le = dle; dz.lb = dlb;
+    dz.a = -(e.P + two * d.dx * z.a * dle) * iw;
+    dz.c = -(e.Q + d.dx * dlm + two * d.dx * z.c * dle) * iw;
+    dz.p0 = -(e.g0 + d.dx * dlm + two * d.dx * z.p0 * dle + two * z.p0 * dlb) * iwb;
+    dz.ph = -(e.gh + d.dx * dlm + two * d.dx * z.ph * dle + two * z.ph * dlb) * iwb;
+    // first trial: the largest t <= 1 keeping both diagonal values of W at >= w_keep times
+    // their current value (W is linear in lambda: alpha(t) = alpha + t 2 dx dlam_e,
+    // beta(t) = beta + t (2 dx dlam_e + 2 dlam_b))
+    T t = T(1);
+    if (o.w_keep > 0.0) {
+      const T da = two * d.dx * dle;
+      const T db = da + two * dlb;
+      if (e.alpha > T(0) && da < T(0)) {
+        const T tm = (T(1) - T(o.w_keep)) * e.alpha / (-da);
+        if (tm < t) t = tm;
+      }
+      if (e.beta > T(0) && db < T(0)) {
+        const T tm = (T(1) - T(o.w_keep)) * e.beta / (-db);
+        if (tm < t) t = tm;
+      }
+    }
+    // Armijo backtracking on phi = 1/2 ||F||^2
+    int nb = 0;
+    bool accepted = false;
+    SliceZ<T> zt;
+    SliceEval<T> et;
+    for (;;) {
+      zt.a = z.a + t * dz.a;     zt.c = z.c + t * dz.c;
+      zt.p0 = z.p0 + t * dz.p0;  zt.ph = z.ph + t * dz.ph;
+      zt.lm = z.lm + t * dz.lm;  zt.le = z.le + t * dz.le;  zt.lb = z.lb + t * dz.lb;
+      slice_eval(d, zt, et);
+      if (et.phi <= (T(1) - T(2) * T(o.c1) * t) * e.phi) { accepted = true; break; }
+      if (nb >= o.max_backtracks) break;
+      nb++;
+      t = t * T(0.5);
+    }
+    R.backtracks += nb;
+    if (!accepted) { R.status = SNAP_SAMPLE_LINESEARCH; break; }
+    z = zt;
+    e = et;
+    R.iters = it + 1;
+  }
+  // second-order sufficient condition at a converged point: inertia of K = (nx, m, 0)
+  if (R.status == SNAP_SAMPLE_OK) {
+    T s00, s01, s02, s11, s12, s22;
+    slice_schur(d, z, e.su, e.su2, e.alpha, e.beta, s00, s01, s02, s11, s12, s22);
+    Ldl3<T> f;
+    if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f) ||
+        !slice_inertia_ok(f, e.alpha, e.beta, nint, m_present, n_absent))
+      R.status = SNAP_SAMPLE_NOT_MINIMUM;
+  }
+  return R;
+}

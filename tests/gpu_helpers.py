@@ -1,0 +1,55 @@
+"""Helpers of the GPU parity tests: run the CUDA path through the C ABI and compare with the
+oracle on the same seeded inputs.
+
+Tolerances (the workload definition): u relative 1e-8 per sample,
+||u_gpu - u_ora||_inf / ||u_ora||_inf; lambda relative 1e-6 per constraint type and sample,
+||dlam_T||_inf / max(||lam_T||_inf, 1e-12); ||h||_inf <= 1e-8 over all nominal rows.
+"""
+import numpy as np
+import torch
+
+from oracle import problems
+from paper_2607_00095_b300 import Problem, decode_stats, options
+
+U_RTOL = 1e-8
+LAM_RTOL = 1e-6
+H_TOL = 1e-8
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def to_dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev())
+
+
+def run_gpu(prob, u_hat, params, u0=None, cache=False, **opt):
+    B = u_hat.shape[0]
+    uh = to_dev(u_hat.reshape(B, -1))
+    pr = to_dev(params)
+    u0d = to_dev(u0.reshape(B, -1)) if u0 is not None else None
+    u, lam, st, cb = prob.project(uh, pr, u0=u0d, opts=options(**opt), cache=cache)
+    torch.cuda.synchronize()
+    return (u.cpu().numpy(), lam.cpu().numpy(), decode_stats(st), cb,
+            dict(uh=uh, pr=pr, u=u, lam=lam, st=st))
+
+
+def assert_u_close(u, ue, rtol=U_RTOL):
+    u = np.atleast_2d(u)
+    ue = np.atleast_2d(ue)
+    for s in range(u.shape[0]):
+        den = max(np.abs(ue[s]).max(), 1e-300)
+        err = np.abs(u[s] - ue[s]).max() / den
+        assert err <= rtol, f"sample {s}: u rel err {err:.3e} > {rtol}"
+
+
+def assert_lam_close(S, lam, le, rtol=LAM_RTOL):
+    lam = np.atleast_2d(lam)
+    le = np.atleast_2d(le)
+    for t in np.unique(S.row_type):
+        sel = S.row_type == t
+        for s in range(lam.shape[0]):
+            den = max(np.abs(le[s, sel]).max(), 1e-12)
+            err = np.abs(lam[s, sel] - le[s, sel]).max() / den
+            assert err <= rtol, f"sample {s} type {problems.ROW_TYPE_NAMES[int(t)]}: lam rel err {err:.3e}"

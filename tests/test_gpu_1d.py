@@ -1,0 +1,182 @@
+"""GPU parity of the 1-D families (A: IC + mass + energy; B: + boundary invariant) against
+the oracle, through the C ABI, on seeded synthetic inputs."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import problems, solve
+from paper_2607_00095_b300 import Problem, _abi, decode_stats, options, synthetic
+from tests import gpu_helpers as H
+from tests import pins_1d
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(family, nx, nt, pr, uh, u0=None, rows=None):
+    u, lam, st, S, b = solve.project_1d(family, nx, nt, pr, uh, u0=u0, nthreads=8)
+    return u, lam, st, S, b
+
+
+@pytest.mark.parametrize("path", ["moment", "general"])
+def test_small_1d_workload_parity(path):
+    w = synthetic.WORKLOADS["small_1d"]
+    nx, nt, B = w["nx"], w["nt"], w["B"]
+    uh, pr = synthetic.gen_1d(w["seed"], B, nx, nt, "A")
+    p = Problem("A", nx, nt)
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    ue, le, so, S, b = _oracle("A", nx, nt, pr, uh)
+    assert (st["status"] == 0).all() and (so["status"] == 0).all()
+    H.assert_u_close(u, ue)
+    H.assert_lam_close(S, lam, le)
+    assert st["h_inf"].max() <= H.H_TOL and st["kkt_inf"].max() <= 1e-10
+    # against the closed form directly
+    uc, lc = pins_1d.family_a_closed_form(nx, nt, pr, uh)
+    H.assert_u_close(u, uc)
+    H.assert_lam_close(S, lam, lc)
+
+
+@pytest.mark.parametrize("path", ["moment", "general"])
+@pytest.mark.parametrize("B,nx,nt,seed", [(6, 128, 21, 11), (3, 96, 7, 12), (2, 100, 9, 13),
+                                          (5, 36, 13, 14), (1, 4, 2, 15), (2, 6, 5, 16),
+                                          (2, 10, 40, 17), (2, 256, 5, 18), (1, 512, 3, 19)])
+def test_burgers_family_parity_ragged(path, B, nx, nt, seed):
+    uh, pr = synthetic.gen_1d(seed, B, nx, nt, "B")
+    p = Problem("B", nx, nt)
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    ue, le, so, S, b = _oracle("B", nx, nt, pr, uh)
+    ok = so["status"] == 0
+    assert ok.any()
+    np.testing.assert_array_equal(st["status"][ok], 0)
+    H.assert_u_close(u[ok], ue[ok])
+    H.assert_lam_close(S, lam[ok], le[ok])
+    assert st["h_inf"][ok].max() <= H.H_TOL
+
+
+def test_burgers_full_size_sampled():
+    """The bench's workload and launch configuration: B=512, nx=128, nt=100, moment path."""
+    w = synthetic.WORKLOADS["burgers_1d"]
+    nx, nt, B = w["nx"], w["nt"], w["B"]
+    uh, pr = synthetic.gen_1d(w["seed"], B, nx, nt, "B")
+    p = Problem("B", nx, nt)
+    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    assert (st["status"] == 0).all()
+    assert st["h_inf"].max() <= H.H_TOL
+    # residual recomputed from the written u, on the GPU and on the host
+    h, hinf = p.residual(d["u"], d["pr"])
+    S = problems.structure_1d("B", nx, nt)
+    b = problems.rhs_1d("B", nx, nt, pr)
+    hh = problems.eval_h(S, u, b)
+    assert np.abs(hh).max() <= H.H_TOL
+    np.testing.assert_allclose(h.cpu().numpy(), hh, atol=1e-13)
+    rng = np.random.default_rng(5)
+    pick = np.sort(rng.choice(B, size=24, replace=False))
+    ue, le, so, S, _ = _oracle("B", nx, nt, pr[pick], uh[pick])
+    assert (so["status"] == 0).all()
+    H.assert_u_close(u[pick], ue)
+    H.assert_lam_close(S, lam[pick], le)
+
+
+def test_moment_and_general_paths_agree():
+    uh, pr = synthetic.gen_1d(21, 16, 128, 33, "B")
+    p = Problem("B", 128, 33)
+    um, lm, sm, _, _ = H.run_gpu(p, uh, pr, path="moment")
+    ug, lg, sg, _, _ = H.run_gpu(p, uh, pr, path="general")
+    ok = (sm["status"] == 0) & (sg["status"] == 0)
+    assert ok.all()
+    H.assert_u_close(um, ug, rtol=1e-12)
+    S = problems.structure_1d("B", 128, 33)
+    H.assert_lam_close(S, lm, lg, rtol=1e-9)
+
+
+def test_general_path_with_start_point():
+    nx, nt, B = 64, 9, 4
+    uh, pr = synthetic.gen_1d(31, B, nx, nt, "B")
+    rng = np.random.default_rng(32)
+    u0 = uh + 0.05 * rng.normal(size=uh.shape)
+    p = Problem("B", nx, nt)
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, u0=u0)          # auto -> general path
+    ue, le, so, S, _ = _oracle("B", nx, nt, pr, uh, u0=u0.reshape(B, -1))
+    ok = so["status"] == 0
+    np.testing.assert_array_equal(st["status"][ok], 0)
+    H.assert_u_close(u[ok], ue[ok])
+    H.assert_lam_close(S, lam[ok], le[ok])
+    with pytest.raises(_abi.SnapError) as ei:
+        H.run_gpu(p, uh, pr, u0=u0, path="moment")
+    assert ei.value.code == 2
+
+
+@pytest.mark.parametrize("rows", [_abi.ROW_IC | _abi.ROW_MASS, _abi.ROW_IC | _abi.ROW_ENERGY,
+                                  _abi.ROW_IC | _abi.ROW_MASS | _abi.ROW_ENERGY])
+@pytest.mark.parametrize("path", ["moment", "general"])
+def test_row_subsets(rows, path):
+    nx, nt, B = 32, 6, 3
+    uh, pr = synthetic.gen_1d(41, B, nx, nt, "A")
+    p = Problem("A", nx, nt, rows=rows)
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    assert (st["status"] == 0).all()
+    U = u.reshape(B, nt, nx)
+    np.testing.assert_allclose(U[:, 0], pr[:, :nx], atol=1e-14)
+    if rows == _abi.ROW_IC | _abi.ROW_MASS:
+        # linear projection: u_k = u_hat_k - mean(u_hat_k) + M
+        M = pr[:, :nx].mean(1)
+        np.testing.assert_allclose(U[:, 1:], uh[:, 1:] - uh[:, 1:].mean(2, keepdims=True) + M[:, None, None],
+                                   atol=1e-13)
+    if rows == _abi.ROW_IC | _abi.ROW_ENERGY:
+        # sphere only: u_k = rho u_hat_k / ||u_hat_k||, rho^2 = E_k / dx
+        t = np.arange(nt) / (nt - 1)
+        E = np.maximum(0.625 * np.exp(-0.5 * t), 0.05)
+        rho = np.sqrt(E / (1.0 / nx))
+        nrm = np.linalg.norm(uh[:, 1:], axis=2, keepdims=True)
+        np.testing.assert_allclose(U[:, 1:], rho[None, 1:, None] * uh[:, 1:] / nrm, atol=1e-12)
+
+
+def test_edge_cases_status_codes():
+    nx, nt, B = 16, 4, 5
+    uh, pr = synthetic.gen_1d(51, B, nx, nt, "B")
+    uh[1, 2, 3] = np.nan                     # sample 1: non-finite target
+    pr[2, nx + 1 + 2] = -0.1                 # sample 2: c_2 < 0, no feasible point
+    pr[3, nx + 1] += 0.5                     # sample 3: c_0 inconsistent with the IC rows
+    p = Problem("B", nx, nt)
+    for path in ("moment", "general"):
+        u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+        assert st["status"][0] == 0 and st["status"][4] == 0
+        assert st["status"][1] == 3          # NONFINITE
+        assert st["status"][2] == 4          # INFEASIBLE_PARAMS
+        assert st["status"][3] == 5          # RESIDUAL
+        assert np.isfinite(u[0]).all()
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, max_iter=1)
+    assert st["status"][0] == 1              # MAXITER
+
+
+def test_empty_batch_and_errors():
+    p = Problem("B", 16, 4)
+    x = torch.zeros(0, 64, dtype=torch.float64, device="cuda")
+    prm = torch.zeros(0, p.n_params, dtype=torch.float64, device="cuda")
+    u, lam, st, _ = p.project(x, prm)
+    assert u.shape[0] == 0
+    with pytest.raises(ValueError):
+        p.project(torch.zeros(2, 64, dtype=torch.float64), torch.zeros(2, p.n_params, dtype=torch.float64))
+
+
+def test_batch_permutation_bitwise_and_determinism():
+    nx, nt, B = 64, 12, 7
+    uh, pr = synthetic.gen_1d(61, B, nx, nt, "B")
+    p = Problem("B", nx, nt)
+    u1, l1, s1, _, _ = H.run_gpu(p, uh, pr)
+    u2, l2, s2, _, _ = H.run_gpu(p, uh, pr)
+    assert np.array_equal(u1, u2) and np.array_equal(l1, l2)
+    perm = np.array([4, 0, 6, 2, 1, 5, 3])
+    u3, l3, s3, _, _ = H.run_gpu(p, uh[perm], pr[perm])
+    assert np.array_equal(u3, u1[perm]) and np.array_equal(l3, l1[perm])
+
+
+def test_residual_entry_point_matches_oracle():
+    nx, nt, B = 48, 7, 3
+    uh, pr = synthetic.gen_1d(71, B, nx, nt, "B")
+    p = Problem("B", nx, nt)
+    x = H.to_dev(uh.reshape(B, -1))
+    h, hinf = p.residual(x, H.to_dev(pr))
+    S = problems.structure_1d("B", nx, nt)
+    he = problems.eval_h(S, uh.reshape(B, -1), problems.rhs_1d("B", nx, nt, pr))
+    np.testing.assert_allclose(h.cpu().numpy(), he, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(hinf.cpu().numpy(), np.abs(he).max(1), rtol=1e-13)
