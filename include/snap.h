@@ -115,7 +115,10 @@ enum {
 enum {
   SNAP_PATH_AUTO = 0,     /* fastest path valid for the call */
   SNAP_PATH_GENERAL = 1,  /* per-element FP64 Newton-KKT (any u0) */
-  SNAP_PATH_MOMENT = 2    /* moment-reduced Newton-KKT, FP64 scalars (u0 = u_hat only) */
+  SNAP_PATH_MOMENT = 2,   /* moment-reduced Newton-KKT, FP64 throughout (u0 = u_hat only) */
+  SNAP_PATH_MIXED = 3     /* moment-reduced Newton-KKT with the moments and the early Newton
+                             steps on the FP32 pipe (float, then double-float), FP64 write
+                             (u0 = u_hat only); AUTO picks it when u0 is NULL */
 };
 
 typedef struct {

@@ -1,0 +1,170 @@
+// Double-float ("double-word") arithmetic on the FP32 pipe: x = hi + lo with two floats,
+// |lo| <= ulp(hi) / 2, about 48 significant bits (relative error ~ 2^-47 per operation).
+//
+// Algorithms: Knuth's TwoSum and Dekker's Fast2Sum for error-free addition, the FMA-based
+// TwoProd for error-free multiplication, and the double-word sum / product / quotient of
+// Joldes, Muller & Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic" (ACM TOMS 44(2), 2017): AccurateDWPlusDW, DWTimesDW and a
+// Newton-corrected quotient.  All float operations are IEEE round-to-nearest (no fast math).
+//
+// Valid while every intermediate stays in [2^-100, 2^100] in magnitude (or is zero); callers
+// check the range of their inputs and fall back to FP64 otherwise.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+// Every function is host + device: the host build runs the same arithmetic in the unit
+// tests of the scalar solver on the CPU.
+#define DF_INL __host__ __device__ __forceinline__
+
+DF_INL float df_d2f(double x) {
+#ifdef __CUDA_ARCH__
+  return __double2float_rn(x);
+#else
+  return (float)x;
+#endif
+}
+
+DF_INL float df_rcp(float x) {
+#ifdef __CUDA_ARCH__
+  return __frcp_rn(x);
+#else
+  return 1.0f / x;
+#endif
+}
+
+struct df64 {
+  float hi, lo;
+  DF_INL df64() {}
+  DF_INL df64(float h, float l) : hi(h), lo(l) {}
+  DF_INL df64(double d) {
+    hi = df_d2f(d);
+    lo = df_d2f(d - (double)hi);
+  }
+  DF_INL explicit df64(int i) : df64((double)i) {}
+  DF_INL explicit operator double() const { return (double)hi + (double)lo; }
+};
+
+DF_INL df64 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return df64(s, e);
+}
+
+DF_INL df64 df_fast_two_sum(float a, float b) {  // requires |a| >= |b|
+  const float s = a + b;
+  const float e = b - (s - a);
+  return df64(s, e);
+}
+
+DF_INL df64 operator+(df64 x, df64 y) {
+  const df64 s = df_two_sum(x.hi, y.hi);
+  const df64 t = df_two_sum(x.lo, y.lo);
+  const df64 v = df_fast_two_sum(s.hi, s.lo + t.hi);
+  return df_fast_two_sum(v.hi, t.lo + v.lo);
+}
+
+DF_INL df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
+DF_INL df64 operator-(df64 x, df64 y) { return x + (-y); }
+
+DF_INL df64 operator*(df64 x, df64 y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+DF_INL df64 operator/(df64 x, df64 y) {
+  const float r = df_rcp(y.hi);
+  const float q1 = x.hi * r;
+  // remainder x - q1 * y, exact in its leading part
+  const float p = q1 * y.hi;
+  const float pe = fmaf(q1, y.hi, -p);
+  const float rem = ((x.hi - p) - pe) + (x.lo - q1 * y.lo);
+  const float q2 = rem * r;
+  return df_fast_two_sum(q1, q2);
+}
+
+DF_INL bool operator<(df64 x, df64 y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+DF_INL bool operator>(df64 x, df64 y) { return y < x; }
+DF_INL bool operator<=(df64 x, df64 y) {
+  return x.hi < y.hi || (x.hi == y.hi && x.lo <= y.lo);
+}
+DF_INL bool operator>=(df64 x, df64 y) { return y <= x; }
+DF_INL bool operator==(df64 x, df64 y) { return x.hi == y.hi && x.lo == y.lo; }
+DF_INL bool operator!=(df64 x, df64 y) { return !(x == y); }
+
+// Accumulate a float pair (h, l) into a double-float sum (used by the moment reductions).
+DF_INL void df_acc(df64 &acc, float h, float l) {
+  const df64 s = df_two_sum(acc.hi, h);
+  acc = df_fast_two_sum(s.hi, s.lo + (acc.lo + l));
+}
+
+// Split a double into a float pair: x = h + l within 2^-48 |x| for 2^-74 <= |x| < 2^57 (and
+// x = 0).  h is x rounded to float; l is the remainder x - h, an integer multiple of ulp(x)
+// that is read off the low words of x and of h widened to double (their difference counts
+// the ulps of x between them), converted to float and scaled by +-ulp(x).  Returns false
+// when x is non-finite or outside that range.
+DF_INL unsigned df_hiword(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2hiint(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return (unsigned)(b >> 32);
+#endif
+}
+DF_INL unsigned df_loword(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2loint(x);
+#else
+  unsigned long long b;
+  memcpy(&b, &x, 8);
+  return (unsigned)b;
+#endif
+}
+DF_INL unsigned df_fbits(float x) {
+#ifdef __CUDA_ARCH__
+  return __float_as_uint(x);
+#else
+  unsigned b;
+  memcpy(&b, &x, 4);
+  return b;
+#endif
+}
+DF_INL float df_bitsf(unsigned b) {
+#ifdef __CUDA_ARCH__
+  return __uint_as_float(b);
+#else
+  float x;
+  memcpy(&x, &b, 4);
+  return x;
+#endif
+}
+DF_INL float df_i2f(int i) {
+#ifdef __CUDA_ARCH__
+  return __int2float_rn(i);
+#else
+  return (float)i;
+#endif
+}
+
+DF_INL bool df_split(double x, float &h, float &l) {
+  const unsigned hw = df_hiword(x);
+  const unsigned lw = df_loword(x);
+  const unsigned e = (hw >> 20) & 0x7FFu;
+  h = df_d2f(x);
+  // low word of h widened to double: float mantissa bits 2..0 land at bits 31..29
+  const int D = (int)(lw - ((df_fbits(h) & 7u) << 29));          // (|x| - |h|) / ulp(x)
+  const float scale = df_bitsf((hw & 0x80000000u) | ((e - 948u) << 23));   // +-ulp(x)
+  l = df_i2f(D) * scale;
+  const bool zero = ((hw & 0x7FFFFFFFu) | lw) == 0u;
+  if (zero) { h = 0.0f; l = 0.0f; }
+  return zero || (e - 949u) <= (1080u - 949u);
+}

@@ -74,7 +74,7 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
     SampleDerived d;
     d.M = g.dx * s1;
     d.E0 = g.dx * s2;
-    d.pad = 0.0;
+    d.q = exp(-pg[g.p_rate] / (double)(g.nt - 1));
     // rows at t = 0 evaluated at u_0 = g
     double hinf = 0.0;
     if (g.rows & SL_MASS) hinf = nan_max(hinf, fabs(g.dx * s1 - d.M));
@@ -151,7 +151,7 @@ enum { KIND_MOMENT = 0, KIND_IC_G = 1, KIND_IC_KEEP = 2, KIND_NONE = 3 };
 __device__ __forceinline__ void slice_factor_at(const SliceIn<double> &d, const SliceZ<double> &z,
                                                 const SliceEval<double> &e, SliceFactor &out) {
   double s00, s01, s02, s11, s12, s22;
-  slice_schur(d, z, e.su, e.su2, e.alpha, e.beta, s00, s01, s02, s11, s12, s22);
+  slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
   Ldl3<double> f;
   if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
     f.d0 = f.d1 = f.d2 = 0.0;
@@ -263,6 +263,7 @@ k1d_moment(Geom1D g, int B, const double *__restrict__ uh, const double *__restr
         d.S1 = m1; d.S2 = m2; d.mx = mmx; d.mn = mmn;
         d.uh0 = row[0]; d.uhh = row[ih];
         d.n = (double)(nx - 2);
+        d.nint = nx - 2;
         d.dx = g.dx;
         d.M = dv.M;
         d.E = (g.rows & SL_ENERGY) ? energy_target(g, dv, pg[g.p_rate], k) : 0.0;
@@ -512,6 +513,7 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
     SliceIn<double> d;
     d.dx = g.dx;
     d.n = (double)(nx - 2);
+    d.nint = nx - 2;
     d.M = dv.M;
     d.E = (g.rows & SL_ENERGY) ? energy_target(g, dv, pg[g.p_rate], k) : 0.0;
     d.C = (g.rows & SL_BOUND) ? pg[g.p_c + k] : 0.0;
@@ -759,6 +761,7 @@ k1d_backward(Geom1D g, int B, const double *__restrict__ gu, const double *__res
     SliceIn<double> d;
     d.dx = g.dx;
     d.n = (double)(nx - 2);
+    d.nint = nx - 2;
     d.rows = g.rows;
     d.M = d.E = d.C = 0.0;
     GenEval<NPL> e;
@@ -926,7 +929,11 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   int launches = 0;
   k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd);
   launches++;
-  if (path == SNAP_PATH_MOMENT) {
+  if (path == SNAP_PATH_MIXED) {
+    const int pid = snap_prof_begin(s, "k1d_mixed");
+    launch_1d_mixed(g, B, u_hat, params, w.sd, u, lambda, w.bst, (SliceFactor *)cache, o, 0, s);
+    snap_prof_end(s, pid);
+  } else if (path == SNAP_PATH_MOMENT) {
     const long long ntiles = ((long long)B * g.nt + 31) / 32;
     long long blocks = (ntiles + 3) / 4;
     if (blocks > 148LL * 64) blocks = 148LL * 64;

@@ -24,8 +24,14 @@
 // Globalisation: Armijo on phi = 1/2 ||F||^2, first trial capped so that W stays positive
 // definite (both of its diagonal values keep >= w_keep of their current value); the
 // second-order condition is checked at the converged point.
+//
+// The scalar type T is double (FP64 pipe), float, or df64 (double-float on the FP32 pipe,
+// df64.cuh).  slice_solve_mixed runs the iteration in float while float steps make reliable
+// progress, then continues in df64 to the FP64 stopping tolerance: the same Newton-KKT
+// iteration, with the early (inexact) steps taken in a cheaper precision.
 #pragma once
 
+#include "df64.cuh"
 #include "snap_internal.h"
 
 template <class T>
@@ -35,6 +41,7 @@ struct SliceIn {
   T n;                // interior count nx - 2
   T dx, M, E, C;      // rhs of the slice rows
   int rows;           // SL_* bits
+  int nint;           // interior count as an integer
 };
 
 template <class T>
@@ -47,15 +54,54 @@ struct SliceEval {
   T alpha, beta, P, Q, su, su2, g0, gh, hm, he, hb, phi, res;
 };
 
+// option values converted once per slice
 template <class T>
-__device__ __forceinline__ T sl_abs(T x) { return x < T(0) ? -x : x; }
+struct SliceOptsT {
+  T tol, c1x2, delta0, w_keep1;   // tol, 2 c1, delta0, 1 - w_keep
+  int max_iter, max_backtracks, max_corrections;
+  bool cap;
+};
 
 template <class T>
-__device__ __forceinline__ T sl_max(T x, T y) { return (x < y) ? y : x; }
+DF_INL T sl_abs(T x) { return x < T(0) ? -x : x; }
 
-// phi and ||F||_inf at z; NaN propagates into res through the comparisons below
 template <class T>
-__device__ __forceinline__ void slice_eval(const SliceIn<T> &d, const SliceZ<T> &z,
+DF_INL T sl_max(T x, T y) { return (x < y) ? y : x; }
+
+DF_INL bool sl_finite(double x) { return isfinite(x); }
+DF_INL bool sl_finite(float x) { return isfinite(x); }
+DF_INL bool sl_finite(df64 x) { return isfinite(x.hi); }
+
+template <class T>
+DF_INL T sl_from(double x);
+template <>
+DF_INL double sl_from<double>(double x) { return x; }
+template <>
+DF_INL float sl_from<float>(double x) { return df_d2f(x); }
+template <>
+DF_INL df64 sl_from<df64>(double x) { return df64(x); }
+
+DF_INL double sl_to_double(double x) { return x; }
+DF_INL double sl_to_double(float x) { return (double)x; }
+DF_INL double sl_to_double(df64 x) { return (double)x; }
+
+template <class T>
+DF_INL SliceOptsT<T> slice_opts(const SolverOpts &o, double tol) {
+  SliceOptsT<T> s;
+  s.tol = sl_from<T>(tol);
+  s.c1x2 = sl_from<T>(2.0 * o.c1);
+  s.delta0 = sl_from<T>(o.delta0);
+  s.w_keep1 = sl_from<T>(1.0 - o.w_keep);
+  s.cap = o.w_keep > 0.0;
+  s.max_iter = o.max_iter;
+  s.max_backtracks = o.max_backtracks;
+  s.max_corrections = o.max_corrections;
+  return s;
+}
+
+// phi and ||F||_inf at z; NaN propagates into res
+template <class T>
+DF_INL void slice_eval(const SliceIn<T> &d, const SliceZ<T> &z,
                                            SliceEval<T> &e) {
   const T two = T(2), one = T(1);
   e.alpha = one + two * d.dx * z.le;
@@ -73,7 +119,7 @@ __device__ __forceinline__ void slice_eval(const SliceIn<T> &d, const SliceZ<T> 
   T gi2 = e.P * e.P * d.S2 + two * e.P * e.Q * d.S1 + e.Q * e.Q * d.n;
   if (gi2 < T(0)) gi2 = T(0);
   const T ginf = sl_max(sl_abs(e.P * d.mx + e.Q), sl_abs(e.P * d.mn + e.Q));
-  e.phi = T(0.5) * (gi2 + e.g0 * e.g0 + e.gh * e.gh + e.hm * e.hm + e.he * e.he + e.hb * e.hb);
+  e.phi = (gi2 + e.g0 * e.g0 + e.gh * e.gh + e.hm * e.hm + e.he * e.he + e.hb * e.hb) * T(0.5f);
   T r = ginf;
   T c;
   c = sl_abs(e.g0); r = (r < c || c != c) ? c : r;
@@ -92,7 +138,7 @@ struct Ldl3 {
 };
 
 template <class T>
-__device__ __forceinline__ bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T s22,
+DF_INL bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T s22,
                                             Ldl3<T> &f) {
   f.d0 = s00;
   if (f.d0 == T(0)) return false;
@@ -107,7 +153,7 @@ __device__ __forceinline__ bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T
 }
 
 template <class T>
-__device__ __forceinline__ void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T &x0, T &x1,
+DF_INL void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T &x0, T &x1,
                                            T &x2) {
   const T y0 = r0;
   const T y1 = r1 - f.l10 * y0;
@@ -120,25 +166,25 @@ __device__ __forceinline__ void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T
 // Schur complement S = J W^-1 J^T of the slice rows at z with W diagonal (w interior, wb at
 // the two boundary points); absent rows get an identity row so their dlam is 0.
 template <class T>
-__device__ __forceinline__ void slice_schur(const SliceIn<T> &d, const SliceZ<T> &z, T su,
-                                            T su2, T w, T wb, T &s00, T &s01, T &s02, T &s11,
+DF_INL void slice_schur(const SliceIn<T> &d, const SliceZ<T> &z, T su,
+                                            T su2, T iw, T iwb, T &s00, T &s01, T &s02, T &s11,
                                             T &s12, T &s22) {
   const T two = T(2), four = T(4);
-  const T iw = T(1) / w, iwb = T(1) / wb;
   const T pp = z.p0 * z.p0 + z.ph * z.ph;
   const T ps = z.p0 + z.ph;
+  const T dx2 = d.dx * d.dx;
   const bool hm = d.rows & SL_MASS, he = d.rows & SL_ENERGY, hb = d.rows & SL_BOUND;
-  s00 = hm ? d.dx * d.dx * (d.n * iw + two * iwb) : T(1);
-  s01 = (hm && he) ? two * d.dx * d.dx * (su * iw + ps * iwb) : T(0);
+  s00 = hm ? dx2 * (d.n * iw + two * iwb) : T(1);
+  s01 = (hm && he) ? two * dx2 * (su * iw + ps * iwb) : T(0);
   s02 = (hm && hb) ? two * d.dx * ps * iwb : T(0);
-  s11 = he ? four * d.dx * d.dx * (su2 * iw + pp * iwb) : T(1);
+  s11 = he ? four * dx2 * (su2 * iw + pp * iwb) : T(1);
   s12 = (he && hb) ? four * d.dx * pp * iwb : T(0);
   s22 = hb ? four * pp * iwb : T(1);
 }
 
 // Inertia test of K via In(W) + In(-S).  nint = interior count, m = rows present.
 template <class T>
-__device__ __forceinline__ bool slice_inertia_ok(const Ldl3<T> &f, T w, T wb, int nint,
+DF_INL bool slice_inertia_ok(const Ldl3<T> &f, T w, T wb, int nint,
                                                  int m_present, int n_absent) {
   if (w == T(0) || wb == T(0)) return false;
   const int npW = (w > T(0) ? nint : 0) + (wb > T(0) ? 2 : 0);
@@ -152,72 +198,85 @@ struct SliceResult {
   int iters, backtracks, status, corrections;
 };
 
-// Run the Newton-KKT iteration of one slice.  z holds the start on entry and the last
-// accepted iterate on exit; e its evaluation.
+// Second-order sufficient condition at z: inertia of K = (nx, m, 0).
 template <class T>
-__device__ inline SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
-                                           const SolverOpts &o) {
-  SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
+DF_INL bool slice_sosc(const SliceIn<T> &d, const SliceZ<T> &z, const SliceEval<T> &e) {
+  const int m_present = ((d.rows & SL_MASS) != 0) + ((d.rows & SL_ENERGY) != 0) +
+                        ((d.rows & SL_BOUND) != 0);
+  if (e.alpha == T(0) || e.beta == T(0)) return false;
+  T s00, s01, s02, s11, s12, s22;
+  slice_schur(d, z, e.su, e.su2, T(1) / e.alpha, T(1) / e.beta, s00, s01, s02, s11, s12, s22);
+  Ldl3<T> f;
+  return ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
+         slice_inertia_ok(f, e.alpha, e.beta, d.nint, m_present, 3 - m_present);
+}
+
+// Newton-KKT iterations from z (already evaluated in e) until e.res <= so.tol, a failure,
+// or `budget` steps; R accumulates counts and receives the status.
+template <class T>
+DF_INL void slice_newton_phase(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
+                                          const SliceOptsT<T> &so, int budget, SliceResult &R) {
   const int m_present = ((d.rows & SL_MASS) != 0) + ((d.rows & SL_ENERGY) != 0) +
                         ((d.rows & SL_BOUND) != 0);
   const int n_absent = 3 - m_present;
-  const int nint = (int)d.n;  // only used for the inertia count
-  slice_eval(d, z, e);
+  const T two = T(2);
   for (int it = 0;; ++it) {
-    if (!(e.res == e.res) || isinf((double)e.res)) { R.status = SNAP_SAMPLE_NONFINITE; break; }
-    if (e.res <= T(o.tol_kkt)) { R.status = SNAP_SAMPLE_OK; break; }
-    if (it >= o.max_iter) { R.status = SNAP_SAMPLE_MAXITER; break; }
+    if (!sl_finite(e.res)) { R.status = SNAP_SAMPLE_NONFINITE; return; }
+    if (e.res <= so.tol) { R.status = SNAP_SAMPLE_OK; return; }
+    if (it >= budget) { R.status = SNAP_SAMPLE_MAXITER; return; }
     // Newton-KKT system.  max_corrections = 0: plain Newton-Raphson (Appendix B); > 0:
     // shift W + delta I until the inertia of K is (nx, m, 0).
     T delta = T(0);
     Ldl3<T> f;
     bool ok = false;
-    T w = e.alpha, wb = e.beta;
-    for (int corr = 0; corr <= o.max_corrections; ++corr) {
-      w = e.alpha + delta;
-      wb = e.beta + delta;
-      T s00, s01, s02, s11, s12, s22;
-      slice_schur(d, z, e.su, e.su2, w, wb, s00, s01, s02, s11, s12, s22);
-      if (w != T(0) && wb != T(0) && ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
-          (o.max_corrections == 0 || slice_inertia_ok(f, w, wb, nint, m_present, n_absent))) {
-        ok = true;
-        break;
+    T iw = T(1), iwb = T(1);
+    for (int corr = 0; corr <= so.max_corrections; ++corr) {
+      const T w = e.alpha + delta, wb = e.beta + delta;
+      if (!(w == T(0)) && !(wb == T(0))) {
+        iw = T(1) / w;
+        iwb = T(1) / wb;
+        T s00, s01, s02, s11, s12, s22;
+        slice_schur(d, z, e.su, e.su2, iw, iwb, s00, s01, s02, s11, s12, s22);
+        if (ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
+            (so.max_corrections == 0 || slice_inertia_ok(f, w, wb, d.nint, m_present, n_absent))) {
+          ok = true;
+          break;
+        }
       }
-      delta = (delta == T(0)) ? T(o.delta0) : delta * T(10);
+      delta = (delta == T(0)) ? so.delta0 : delta * T(10);
       R.corrections++;
     }
-    if (!ok) { R.status = SNAP_SAMPLE_SINGULAR; break; }
+    if (!ok) { R.status = SNAP_SAMPLE_SINGULAR; return; }
     // rhs r = h - J W^-1 grad L
-    const T two = T(2);
-    const T iw = T(1) / w, iwb = T(1) / wb;
     const T sg = e.P * d.S1 + e.Q * d.n;                                     // sum_int gL
     const T sug = z.a * e.P * d.S2 + (z.a * e.Q + z.c * e.P) * d.S1 + z.c * e.Q * d.n;
     const T pg = z.p0 * e.g0 + z.ph * e.gh;
-    T r0 = (d.rows & SL_MASS) ? e.hm - d.dx * (sg * iw + (e.g0 + e.gh) * iwb) : T(0);
-    T r1 = (d.rows & SL_ENERGY) ? e.he - two * d.dx * (sug * iw + pg * iwb) : T(0);
-    T r2 = (d.rows & SL_BOUND) ? e.hb - two * pg * iwb : T(0);
+    const T r0 = (d.rows & SL_MASS) ? e.hm - d.dx * (sg * iw + (e.g0 + e.gh) * iwb) : T(0);
+    const T r1 = (d.rows & SL_ENERGY) ? e.he - two * d.dx * (sug * iw + pg * iwb) : T(0);
+    const T r2 = (d.rows & SL_BOUND) ? e.hb - two * pg * iwb : T(0);
     T dlm, dle, dlb;
     ldl3_solve(f, r0, r1, r2, dlm, dle, dlb);
     // du = -W^-1 (grad L + J^T dlam)
     SliceZ<T> dz;
     dz.lm = dlm; dz.le = dle; dz.lb = dlb;
-    dz.a = -(e.P + two * d.dx * z.a * dle) * iw;
-    dz.c = -(e.Q + d.dx * dlm + two * d.dx * z.c * dle) * iw;
-    dz.p0 = -(e.g0 + d.dx * dlm + two * d.dx * z.p0 * dle + two * z.p0 * dlb) * iwb;
-    dz.ph = -(e.gh + d.dx * dlm + two * d.dx * z.ph * dle + two * z.ph * dlb) * iwb;
+    const T dxlm = d.dx * dlm, dxle2 = two * d.dx * dle;
+    dz.a = -(e.P + dxle2 * z.a) * iw;
+    dz.c = -(e.Q + dxlm + dxle2 * z.c) * iw;
+    dz.p0 = -(e.g0 + dxlm + (dxle2 + two * dlb) * z.p0) * iwb;
+    dz.ph = -(e.gh + dxlm + (dxle2 + two * dlb) * z.ph) * iwb;
     // first trial: the largest t <= 1 keeping both diagonal values of W at >= w_keep times
     // their current value (W is linear in lambda: alpha(t) = alpha + t 2 dx dlam_e,
     // beta(t) = beta + t (2 dx dlam_e + 2 dlam_b))
     T t = T(1);
-    if (o.w_keep > 0.0) {
-      const T da = two * d.dx * dle;
+    if (so.cap) {
+      const T da = dxle2;
       const T db = da + two * dlb;
       if (e.alpha > T(0) && da < T(0)) {
-        const T tm = (T(1) - T(o.w_keep)) * e.alpha / (-da);
+        const T tm = so.w_keep1 * e.alpha / (-da);
         if (tm < t) t = tm;
       }
       if (e.beta > T(0) && db < T(0)) {
-        const T tm = (T(1) - T(o.w_keep)) * e.beta / (-db);
+        const T tm = so.w_keep1 * e.beta / (-db);
         if (tm < t) t = tm;
       }
     }
@@ -231,25 +290,83 @@ __device__ inline SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, Sl
       zt.p0 = z.p0 + t * dz.p0;  zt.ph = z.ph + t * dz.ph;
       zt.lm = z.lm + t * dz.lm;  zt.le = z.le + t * dz.le;  zt.lb = z.lb + t * dz.lb;
       slice_eval(d, zt, et);
-      if (et.phi <= (T(1) - T(2) * T(o.c1) * t) * e.phi) { accepted = true; break; }
-      if (nb >= o.max_backtracks) break;
+      if (et.phi <= (T(1) - so.c1x2 * t) * e.phi) { accepted = true; break; }
+      if (nb >= so.max_backtracks) break;
       nb++;
-      t = t * T(0.5);
+      t = t * T(0.5f);
     }
     R.backtracks += nb;
-    if (!accepted) { R.status = SNAP_SAMPLE_LINESEARCH; break; }
+    if (!accepted) { R.status = SNAP_SAMPLE_LINESEARCH; return; }
     z = zt;
     e = et;
-    R.iters = it + 1;
+    R.iters++;
   }
-  // second-order sufficient condition at a converged point: inertia of K = (nx, m, 0)
-  if (R.status == SNAP_SAMPLE_OK) {
-    T s00, s01, s02, s11, s12, s22;
-    slice_schur(d, z, e.su, e.su2, e.alpha, e.beta, s00, s01, s02, s11, s12, s22);
-    Ldl3<T> f;
-    if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f) ||
-        !slice_inertia_ok(f, e.alpha, e.beta, nint, m_present, n_absent))
-      R.status = SNAP_SAMPLE_NOT_MINIMUM;
+}
+
+// The whole iteration in one precision T (FP64 reference path).
+template <class T>
+DF_INL SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
+                                           const SolverOpts &o) {
+  SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
+  const SliceOptsT<T> so = slice_opts<T>(o, o.tol_kkt);
+  slice_eval(d, z, e);
+  slice_newton_phase(d, z, e, so, o.max_iter, R);
+  if (R.status == SNAP_SAMPLE_OK && !slice_sosc(d, z, e)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
+  return R;
+}
+
+template <class T, class S>
+DF_INL SliceIn<T> slice_in_cast(const SliceIn<S> &s) {
+  SliceIn<T> d;
+  d.S1 = sl_from<T>(sl_to_double(s.S1)); d.S2 = sl_from<T>(sl_to_double(s.S2));
+  d.mx = sl_from<T>(sl_to_double(s.mx)); d.mn = sl_from<T>(sl_to_double(s.mn));
+  d.uh0 = sl_from<T>(sl_to_double(s.uh0)); d.uhh = sl_from<T>(sl_to_double(s.uhh));
+  d.n = sl_from<T>(sl_to_double(s.n)); d.dx = sl_from<T>(sl_to_double(s.dx));
+  d.M = sl_from<T>(sl_to_double(s.M)); d.E = sl_from<T>(sl_to_double(s.E));
+  d.C = sl_from<T>(sl_to_double(s.C));
+  d.rows = s.rows;
+  d.nint = s.nint;
+  return d;
+}
+
+DF_INL df64 df_from_float(float x) { return df64(x, 0.0f); }
+
+// Mixed precision: float steps while they make reliable progress, then df64 steps to
+// o.tol_kkt.  The float phase stops when ||F||_inf <= max(1e-5 ||F(z0)||_inf, 1e-6 * scale)
+// (scale = the largest magnitude among the slice data; float rounding puts a floor near
+// 1e-7 * scale under ||F||), when a line search needs more than 8 halvings (the float merit
+// is then at its rounding floor), or after half of the iteration budget.  dd holds the
+// inputs in df64; the result z is returned in df64.
+DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
+                                     SliceEval<df64> &e, const SolverOpts &o) {
+  SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
+  SliceIn<float> d32;
+  d32.S1 = dd.S1.hi; d32.S2 = dd.S2.hi; d32.mx = dd.mx.hi; d32.mn = dd.mn.hi;
+  d32.uh0 = dd.uh0.hi; d32.uhh = dd.uhh.hi; d32.n = dd.n.hi; d32.dx = dd.dx.hi;
+  d32.M = dd.M.hi; d32.E = dd.E.hi; d32.C = dd.C.hi;
+  d32.rows = dd.rows;
+  d32.nint = dd.nint;
+  SliceZ<float> z32{z.a.hi, z.c.hi, z.p0.hi, z.ph.hi, z.lm.hi, z.le.hi, z.lb.hi};
+  SliceEval<float> e32;
+  slice_eval(d32, z32, e32);
+  if (sl_finite(e32.res)) {
+    SliceOptsT<float> s32 = slice_opts<float>(o, o.tol_kkt);
+    s32.max_backtracks = o.max_backtracks < 8 ? o.max_backtracks : 8;
+    float scale = fmaxf(fmaxf(fabsf(d32.mx), fabsf(d32.mn)), fmaxf(fabsf(d32.uh0), fabsf(d32.uhh)));
+    scale = fmaxf(scale, fmaxf(fabsf(d32.M), sqrtf(fabsf(d32.E) + fabsf(d32.C))));
+    float tol32 = fmaxf(1e-5f * e32.res, 1e-6f * scale);
+    if (tol32 > s32.tol) s32.tol = tol32;
+    slice_newton_phase(d32, z32, e32, s32, o.max_iter / 2, R);
+    if (R.status != SNAP_SAMPLE_NONFINITE) {
+      z.a = df_from_float(z32.a); z.c = df_from_float(z32.c);
+      z.p0 = df_from_float(z32.p0); z.ph = df_from_float(z32.ph);
+      z.lm = df_from_float(z32.lm); z.le = df_from_float(z32.le); z.lb = df_from_float(z32.lb);
+    }
   }
+  R.status = SNAP_SAMPLE_OK;
+  const SliceOptsT<df64> sd = slice_opts<df64>(o, o.tol_kkt);
+  slice_eval(dd, z, e);
+  slice_newton_phase(dd, z, e, sd, o.max_iter - R.iters, R);
+  if (R.status == SNAP_SAMPLE_OK && !slice_sosc(dd, z, e)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
   return R;
 }

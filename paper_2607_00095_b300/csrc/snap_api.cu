@@ -48,7 +48,7 @@ snap_status check_opts(const snap_options &o) {
       o.max_backtracks < 0 || o.max_backtracks > 200 ||
       !(o.armijo_c1 > 0.0 && o.armijo_c1 < 0.5) || !(o.delta0 > 0.0) || o.max_corrections < 0 ||
       o.max_corrections > 100 ||
-      o.path < SNAP_PATH_AUTO || o.path > SNAP_PATH_MOMENT || !(o.w_keep >= 0.0 && o.w_keep < 1.0))
+      o.path < SNAP_PATH_AUTO || o.path > SNAP_PATH_MIXED || !(o.w_keep >= 0.0 && o.w_keep < 1.0))
     return fail(SNAP_ERR_INVALID_ARG, "invalid snap_options");
   return SNAP_OK;
 }
@@ -348,9 +348,9 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
   if (!workspace || workspace_bytes < need)
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   int path = o.path;
-  if (path == SNAP_PATH_MOMENT && u0 && u0 != u_hat)
-    return fail(SNAP_ERR_UNSUPPORTED, "the moment path needs u0 = u_hat");
-  if (path == SNAP_PATH_AUTO) path = (u0 && u0 != u_hat) ? SNAP_PATH_GENERAL : SNAP_PATH_MOMENT;
+  if ((path == SNAP_PATH_MOMENT || path == SNAP_PATH_MIXED) && u0 && u0 != u_hat)
+    return fail(SNAP_ERR_UNSUPPORTED, "the moment paths need u0 = u_hat");
+  if (path == SNAP_PATH_AUTO) path = (u0 && u0 != u_hat) ? SNAP_PATH_GENERAL : SNAP_PATH_MIXED;
   if (u0 == u_hat) u0 = nullptr;
   const SolverOpts so = to_solver(o);
   cudaError_t e;

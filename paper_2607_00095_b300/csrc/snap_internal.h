@@ -57,7 +57,7 @@ struct Geom1D {
 //   BwdContrib[B*nt]  per-slice backward contributions
 //   double[B*nt]      per-slice residual maxima
 struct SampleDerived {
-  double M, E0, h0_inf, pad;
+  double M, E0, h0_inf, q;   // q = exp(-r dt): E0 exp(-r t_k) = E0 q^k
 };
 
 // Per-slice contributions of the backward pass to dL/dtheta (summed per sample):
@@ -105,6 +105,9 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
                                const double *params, double *h, double *h_inf, void *ws,
                                cudaStream_t s);
 size_t ws_bytes_1d(const snap_problem *p, int B);
+void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *params,
+                     const SampleDerived *sd, double *u, double *lambda, BlockStat *bst,
+                     SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s);
 
 cudaError_t setup_2d(snap_problem *p);
 void teardown_2d(snap_problem *p);

@@ -17,7 +17,10 @@ def _oracle(family, nx, nt, pr, uh, u0=None, rows=None):
     return u, lam, st, S, b
 
 
-@pytest.mark.parametrize("path", ["moment", "general"])
+PATHS = ["mixed", "moment", "general"]
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_small_1d_workload_parity(path):
     w = synthetic.WORKLOADS["small_1d"]
     nx, nt, B = w["nx"], w["nt"], w["B"]
@@ -35,7 +38,7 @@ def test_small_1d_workload_parity(path):
     H.assert_lam_close(S, lam, lc)
 
 
-@pytest.mark.parametrize("path", ["moment", "general"])
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("B,nx,nt,seed", [(6, 128, 21, 11), (3, 96, 7, 12), (2, 100, 9, 13),
                                           (5, 36, 13, 14), (1, 4, 2, 15), (2, 6, 5, 16),
                                           (2, 10, 40, 17), (2, 256, 5, 18), (1, 512, 3, 19)])
@@ -76,16 +79,38 @@ def test_burgers_full_size_sampled():
     H.assert_lam_close(S, lam[pick], le)
 
 
-def test_moment_and_general_paths_agree():
+def test_paths_agree():
     uh, pr = synthetic.gen_1d(21, 16, 128, 33, "B")
     p = Problem("B", 128, 33)
     um, lm, sm, _, _ = H.run_gpu(p, uh, pr, path="moment")
     ug, lg, sg, _, _ = H.run_gpu(p, uh, pr, path="general")
-    ok = (sm["status"] == 0) & (sg["status"] == 0)
-    assert ok.all()
-    H.assert_u_close(um, ug, rtol=1e-12)
+    ux, lx, sx, _, _ = H.run_gpu(p, uh, pr, path="mixed")
+    assert (sm["status"] == 0).all() and (sg["status"] == 0).all() and (sx["status"] == 0).all()
     S = problems.structure_1d("B", 128, 33)
+    # the two FP64 paths run the same iteration: agreement to rounding
+    H.assert_u_close(um, ug, rtol=1e-12)
     H.assert_lam_close(S, lm, lg, rtol=1e-9)
+    # the mixed path converges to the same KKT point from float / double-float steps; both
+    # stop inside ||F||_inf <= 1e-10, so they agree to the workload tolerances, not to rounding
+    H.assert_u_close(ux, um)
+    H.assert_lam_close(S, lx, lm)
+
+
+def test_mixed_path_falls_back_to_fp64_out_of_range():
+    """Samples scaled far outside the float-pair range take the FP64 fallback."""
+    nx, nt, B = 64, 6, 4
+    uh, pr = synthetic.gen_1d(25, B, nx, nt, "B")
+    for s, scale in ((1, 1e20), (2, 1e-26)):
+        uh[s] *= scale
+        pr[s, :nx] *= scale
+        pr[s, nx + 1:] *= scale * scale
+    p = Problem("B", nx, nt)
+    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path="mixed")
+    ue, le, so, S, _ = _oracle("B", nx, nt, pr, uh)
+    ok = so["status"] == 0
+    assert ok[[0, 3]].all()
+    np.testing.assert_array_equal(st["status"][ok], so["status"][ok])
+    H.assert_u_close(u[ok], ue[ok])
 
 
 def test_general_path_with_start_point():
@@ -107,7 +132,7 @@ def test_general_path_with_start_point():
 
 @pytest.mark.parametrize("rows", [_abi.ROW_IC | _abi.ROW_MASS, _abi.ROW_IC | _abi.ROW_ENERGY,
                                   _abi.ROW_IC | _abi.ROW_MASS | _abi.ROW_ENERGY])
-@pytest.mark.parametrize("path", ["moment", "general"])
+@pytest.mark.parametrize("path", PATHS)
 def test_row_subsets(rows, path):
     nx, nt, B = 32, 6, 3
     uh, pr = synthetic.gen_1d(41, B, nx, nt, "A")
@@ -137,7 +162,7 @@ def test_edge_cases_status_codes():
     pr[2, nx + 1 + 2] = -0.1                 # sample 2: c_2 < 0, no feasible point
     pr[3, nx + 1] += 0.5                     # sample 3: c_0 inconsistent with the IC rows
     p = Problem("B", nx, nt)
-    for path in ("moment", "general"):
+    for path in PATHS:
         u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
         assert st["status"][0] == 0 and st["status"][4] == 0
         assert st["status"][1] == 3          # NONFINITE
