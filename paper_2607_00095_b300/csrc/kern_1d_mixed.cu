@@ -49,7 +49,7 @@ __device__ __forceinline__ df64 shfl_df(df64 v, int off) {
   return df64(__shfl_xor_sync(FULL, v.hi, off), __shfl_xor_sync(FULL, v.lo, off));
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
           const SampleDerived *__restrict__ sd, double *__restrict__ u,
           double *__restrict__ lam, BlockStat *__restrict__ bst,

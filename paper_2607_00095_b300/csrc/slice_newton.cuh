@@ -211,75 +211,113 @@ DF_INL bool slice_sosc(const SliceIn<T> &d, const SliceZ<T> &z, const SliceEval<
          slice_inertia_ok(f, e.alpha, e.beta, d.nint, m_present, 3 - m_present);
 }
 
-// Newton-KKT iterations from z (already evaluated in e) until e.res <= so.tol, a failure,
-// or `budget` steps; R accumulates counts and receives the status.
-template <class T>
-DF_INL void slice_newton_phase(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
-                                          const SliceOptsT<T> &so, int budget, SliceResult &R) {
+template <class L, class T>
+DF_INL L sl_cast(T x);
+template <>
+DF_INL double sl_cast<double, double>(double x) { return x; }
+template <>
+DF_INL float sl_cast<float, float>(float x) { return x; }
+template <>
+DF_INL float sl_cast<float, df64>(df64 x) { return x.hi; }
+template <>
+DF_INL df64 sl_cast<df64, float>(float x) { return df64(x, 0.0f); }
+template <>
+DF_INL df64 sl_cast<df64, df64>(df64 x) { return x; }
+
+// Newton-KKT direction at z in precision L: solve S dlam = h - J W^-1 grad L and form
+// du = -W^-1 (grad L + J^T dlam) from the residual components of e.  Returns false when
+// the Schur complement is singular (or cannot be corrected).
+template <class L>
+DF_INL bool slice_direction(const SliceIn<L> &d, const SliceZ<L> &z, const SliceEval<L> &e,
+                            int max_corrections, L delta0, SliceZ<L> &dz, int &corrections) {
   const int m_present = ((d.rows & SL_MASS) != 0) + ((d.rows & SL_ENERGY) != 0) +
                         ((d.rows & SL_BOUND) != 0);
-  const int n_absent = 3 - m_present;
-  const T two = T(2);
+  const L two = L(2);
+  L delta = L(0);
+  Ldl3<L> f;
+  bool ok = false;
+  L iw = L(1), iwb = L(1);
+  // max_corrections = 0: plain Newton-Raphson (Appendix B); > 0: shift W + delta I until
+  // the inertia of K is (nx, m, 0)
+  for (int corr = 0; corr <= max_corrections; ++corr) {
+    const L w = e.alpha + delta, wb = e.beta + delta;
+    if (!(w == L(0)) && !(wb == L(0))) {
+      iw = L(1) / w;
+      iwb = L(1) / wb;
+      L s00, s01, s02, s11, s12, s22;
+      slice_schur(d, z, e.su, e.su2, iw, iwb, s00, s01, s02, s11, s12, s22);
+      if (ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
+          (max_corrections == 0 || slice_inertia_ok(f, w, wb, d.nint, m_present, 3 - m_present))) {
+        ok = true;
+        break;
+      }
+    }
+    delta = (delta == L(0)) ? delta0 : delta * L(10);
+    corrections++;
+  }
+  if (!ok) return false;
+  const L sg = e.P * d.S1 + e.Q * d.n;                                     // sum_int gL
+  const L sug = z.a * e.P * d.S2 + (z.a * e.Q + z.c * e.P) * d.S1 + z.c * e.Q * d.n;
+  const L pg = z.p0 * e.g0 + z.ph * e.gh;
+  const L r0 = (d.rows & SL_MASS) ? e.hm - d.dx * (sg * iw + (e.g0 + e.gh) * iwb) : L(0);
+  const L r1 = (d.rows & SL_ENERGY) ? e.he - two * d.dx * (sug * iw + pg * iwb) : L(0);
+  const L r2 = (d.rows & SL_BOUND) ? e.hb - two * pg * iwb : L(0);
+  L dlm, dle, dlb;
+  ldl3_solve(f, r0, r1, r2, dlm, dle, dlb);
+  dz.lm = dlm; dz.le = dle; dz.lb = dlb;
+  const L dxlm = d.dx * dlm, dxle2 = two * d.dx * dle;
+  dz.a = -(e.P + dxle2 * z.a) * iw;
+  dz.c = -(e.Q + dxlm + dxle2 * z.c) * iw;
+  dz.p0 = -(e.g0 + dxlm + (dxle2 + two * dlb) * z.p0) * iwb;
+  dz.ph = -(e.gh + dxlm + (dxle2 + two * dlb) * z.ph) * iwb;
+  return true;
+}
+
+// Newton-KKT iterations from z (already evaluated in e) until e.res <= so.tol, a failure,
+// or `budget` steps; R accumulates counts and receives the status.  F and the merit are
+// evaluated in T; the Newton system is assembled and solved in L (L = T: plain Newton;
+// L = float with T = df64: Newton steps solved in float against a double-float residual,
+// i.e. mixed-precision iterative refinement of the step).
+template <class T, class L>
+DF_INL void slice_newton_phase(const SliceIn<T> &d, const SliceIn<L> &dl, SliceZ<T> &z,
+                               SliceEval<T> &e, const SliceOptsT<T> &so, const SliceOptsT<L> &sl,
+                               int budget, SliceResult &R) {
   for (int it = 0;; ++it) {
     if (!sl_finite(e.res)) { R.status = SNAP_SAMPLE_NONFINITE; return; }
     if (e.res <= so.tol) { R.status = SNAP_SAMPLE_OK; return; }
     if (it >= budget) { R.status = SNAP_SAMPLE_MAXITER; return; }
-    // Newton-KKT system.  max_corrections = 0: plain Newton-Raphson (Appendix B); > 0:
-    // shift W + delta I until the inertia of K is (nx, m, 0).
-    T delta = T(0);
-    Ldl3<T> f;
-    bool ok = false;
-    T iw = T(1), iwb = T(1);
-    for (int corr = 0; corr <= so.max_corrections; ++corr) {
-      const T w = e.alpha + delta, wb = e.beta + delta;
-      if (!(w == T(0)) && !(wb == T(0))) {
-        iw = T(1) / w;
-        iwb = T(1) / wb;
-        T s00, s01, s02, s11, s12, s22;
-        slice_schur(d, z, e.su, e.su2, iw, iwb, s00, s01, s02, s11, s12, s22);
-        if (ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
-            (so.max_corrections == 0 || slice_inertia_ok(f, w, wb, d.nint, m_present, n_absent))) {
-          ok = true;
-          break;
-        }
-      }
-      delta = (delta == T(0)) ? so.delta0 : delta * T(10);
-      R.corrections++;
+    SliceZ<L> zl{sl_cast<L>(z.a), sl_cast<L>(z.c), sl_cast<L>(z.p0), sl_cast<L>(z.ph),
+                 sl_cast<L>(z.lm), sl_cast<L>(z.le), sl_cast<L>(z.lb)};
+    SliceEval<L> el;
+    el.alpha = sl_cast<L>(e.alpha); el.beta = sl_cast<L>(e.beta);
+    el.P = sl_cast<L>(e.P); el.Q = sl_cast<L>(e.Q);
+    el.su = sl_cast<L>(e.su); el.su2 = sl_cast<L>(e.su2);
+    el.g0 = sl_cast<L>(e.g0); el.gh = sl_cast<L>(e.gh);
+    el.hm = sl_cast<L>(e.hm); el.he = sl_cast<L>(e.he); el.hb = sl_cast<L>(e.hb);
+    SliceZ<L> dzl;
+    if (!slice_direction(dl, zl, el, sl.max_corrections, sl.delta0, dzl, R.corrections)) {
+      R.status = SNAP_SAMPLE_SINGULAR;
+      return;
     }
-    if (!ok) { R.status = SNAP_SAMPLE_SINGULAR; return; }
-    // rhs r = h - J W^-1 grad L
-    const T sg = e.P * d.S1 + e.Q * d.n;                                     // sum_int gL
-    const T sug = z.a * e.P * d.S2 + (z.a * e.Q + z.c * e.P) * d.S1 + z.c * e.Q * d.n;
-    const T pg = z.p0 * e.g0 + z.ph * e.gh;
-    const T r0 = (d.rows & SL_MASS) ? e.hm - d.dx * (sg * iw + (e.g0 + e.gh) * iwb) : T(0);
-    const T r1 = (d.rows & SL_ENERGY) ? e.he - two * d.dx * (sug * iw + pg * iwb) : T(0);
-    const T r2 = (d.rows & SL_BOUND) ? e.hb - two * pg * iwb : T(0);
-    T dlm, dle, dlb;
-    ldl3_solve(f, r0, r1, r2, dlm, dle, dlb);
-    // du = -W^-1 (grad L + J^T dlam)
-    SliceZ<T> dz;
-    dz.lm = dlm; dz.le = dle; dz.lb = dlb;
-    const T dxlm = d.dx * dlm, dxle2 = two * d.dx * dle;
-    dz.a = -(e.P + dxle2 * z.a) * iw;
-    dz.c = -(e.Q + dxlm + dxle2 * z.c) * iw;
-    dz.p0 = -(e.g0 + dxlm + (dxle2 + two * dlb) * z.p0) * iwb;
-    dz.ph = -(e.gh + dxlm + (dxle2 + two * dlb) * z.ph) * iwb;
     // first trial: the largest t <= 1 keeping both diagonal values of W at >= w_keep times
     // their current value (W is linear in lambda: alpha(t) = alpha + t 2 dx dlam_e,
     // beta(t) = beta + t (2 dx dlam_e + 2 dlam_b))
-    T t = T(1);
-    if (so.cap) {
-      const T da = dxle2;
-      const T db = da + two * dlb;
-      if (e.alpha > T(0) && da < T(0)) {
-        const T tm = so.w_keep1 * e.alpha / (-da);
-        if (tm < t) t = tm;
+    L tl = L(1);
+    if (sl.cap) {
+      const L da = L(2) * dl.dx * dzl.le;
+      const L db = da + L(2) * dzl.lb;
+      if (el.alpha > L(0) && da < L(0)) {
+        const L tm = sl.w_keep1 * el.alpha / (-da);
+        if (tm < tl) tl = tm;
       }
-      if (e.beta > T(0) && db < T(0)) {
-        const T tm = so.w_keep1 * e.beta / (-db);
-        if (tm < t) t = tm;
+      if (el.beta > L(0) && db < L(0)) {
+        const L tm = sl.w_keep1 * el.beta / (-db);
+        if (tm < tl) tl = tm;
       }
     }
+    const SliceZ<T> dz{sl_cast<T>(dzl.a), sl_cast<T>(dzl.c), sl_cast<T>(dzl.p0), sl_cast<T>(dzl.ph),
+                       sl_cast<T>(dzl.lm), sl_cast<T>(dzl.le), sl_cast<T>(dzl.lb)};
+    T t = sl_cast<T>(tl);
     // Armijo backtracking on phi = 1/2 ||F||^2
     int nb = 0;
     bool accepted = false;
@@ -310,7 +348,7 @@ DF_INL SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> 
   SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
   const SliceOptsT<T> so = slice_opts<T>(o, o.tol_kkt);
   slice_eval(d, z, e);
-  slice_newton_phase(d, z, e, so, o.max_iter, R);
+  slice_newton_phase<T, T>(d, d, z, e, so, so, o.max_iter, R);
   if (R.status == SNAP_SAMPLE_OK && !slice_sosc(d, z, e)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
   return R;
 }
@@ -331,8 +369,9 @@ DF_INL SliceIn<T> slice_in_cast(const SliceIn<S> &s) {
 
 DF_INL df64 df_from_float(float x) { return df64(x, 0.0f); }
 
-// Mixed precision: float steps while they make reliable progress, then df64 steps to
-// o.tol_kkt.  The float phase stops when ||F||_inf <= max(1e-5 ||F(z0)||_inf, 1e-6 * scale)
+// Mixed precision: float steps while they make reliable progress, then steps whose residual
+// F and merit are evaluated in df64 while the Newton system is still solved in float
+// (iterative refinement of the Newton step), to o.tol_kkt.  The float phase stops when ||F||_inf <= max(1e-5 ||F(z0)||_inf, 1e-6 * scale)
 // (scale = the largest magnitude among the slice data; float rounding puts a floor near
 // 1e-7 * scale under ||F||), when a line search needs more than 8 halvings (the float merit
 // is then at its rounding floor), or after half of the iteration budget.  dd holds the
@@ -356,7 +395,7 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
     scale = fmaxf(scale, fmaxf(fabsf(d32.M), sqrtf(fabsf(d32.E) + fabsf(d32.C))));
     float tol32 = fmaxf(1e-5f * e32.res, 1e-6f * scale);
     if (tol32 > s32.tol) s32.tol = tol32;
-    slice_newton_phase(d32, z32, e32, s32, o.max_iter / 2, R);
+    slice_newton_phase<float, float>(d32, d32, z32, e32, s32, s32, o.max_iter / 2, R);
     if (R.status != SNAP_SAMPLE_NONFINITE) {
       z.a = df_from_float(z32.a); z.c = df_from_float(z32.c);
       z.p0 = df_from_float(z32.p0); z.ph = df_from_float(z32.ph);
@@ -365,8 +404,15 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
   }
   R.status = SNAP_SAMPLE_OK;
   const SliceOptsT<df64> sd = slice_opts<df64>(o, o.tol_kkt);
+  const SliceOptsT<float> sf = slice_opts<float>(o, o.tol_kkt);
   slice_eval(dd, z, e);
-  slice_newton_phase(dd, z, e, sd, o.max_iter - R.iters, R);
-  if (R.status == SNAP_SAMPLE_OK && !slice_sosc(dd, z, e)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
+  slice_newton_phase<df64, float>(dd, d32, z, e, sd, sf, o.max_iter - R.iters, R);
+  if (R.status == SNAP_SAMPLE_OK) {
+    // second-order check on the float image of the converged point (a sign test)
+    SliceZ<float> zf{z.a.hi, z.c.hi, z.p0.hi, z.ph.hi, z.lm.hi, z.le.hi, z.lb.hi};
+    SliceEval<float> ef;
+    slice_eval(d32, zf, ef);
+    if (!slice_sosc(d32, zf, ef)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
+  }
   return R;
 }
