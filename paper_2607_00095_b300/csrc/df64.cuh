@@ -44,7 +44,7 @@ struct df64 {
     lo = df_d2f(d - (double)hi);
   }
   DF_INL explicit df64(int i) : df64((double)i) {}
-  DF_INL explicit operator double() const { return (double)hi + (double)lo; }
+  DF_INL explicit operator double() const;
 };
 
 DF_INL df64 df_two_sum(float a, float b) {
@@ -168,3 +168,22 @@ DF_INL bool df_split(double x, float &h, float &l) {
   if (zero) { h = 0.0f; l = 0.0f; }
   return zero || (e - 949u) <= (1080u - 949u);
 }
+
+// float -> double by integer bit construction (normal floats and zero; other values go
+// through the conversion instruction)
+DF_INL double df_f2d(float f) {
+#ifdef __CUDA_ARCH__
+  const unsigned b = __float_as_uint(f);
+  const unsigned ef = (b >> 23) & 0xFFu;
+  if (ef == 0u || ef == 0xFFu) return (double)f;
+  const unsigned hi = (b & 0x80000000u) | ((ef + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  const unsigned lo = (b & 7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+#else
+  return (double)f;
+#endif
+}
+
+// df64 -> double with a single FP64 addition
+DF_INL double df_to_double(df64 x) { return df_f2d(x.hi) + df_f2d(x.lo); }
+DF_INL df64::operator double() const { return df_to_double(*this); }

@@ -57,7 +57,9 @@ __device__ __forceinline__ double energy_target(const Geom1D &g, const SampleDer
 // t = 0 rows that the IC rows imply (left out of the solve).  One warp per sample.
 // ---------------------------------------------------------------------------------------
 __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
-                           SampleDerived *__restrict__ sd) {
+                           SampleDerived *__restrict__ sd, const double *__restrict__ ic_uh,
+                           double *__restrict__ ic_u, double *__restrict__ ic_lam,
+                           BlockStat *__restrict__ ic_bst, double tol_kkt) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= B) return;
@@ -75,6 +77,11 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
     d.M = g.dx * s1;
     d.E0 = g.dx * s2;
     d.q = exp(-pg[g.p_rate] / (double)(g.nt - 1));
+    const double fl = d.M * d.M + g.energy_floor;
+    d.Mh = __double2float_rn(d.M);   d.Ml = __double2float_rn(d.M - (double)d.Mh);
+    d.E0h = __double2float_rn(d.E0); d.E0l = __double2float_rn(d.E0 - (double)d.E0h);
+    d.qh = __double2float_rn(d.q);   d.ql = __double2float_rn(d.q - (double)d.qh);
+    d.fh = __double2float_rn(fl);    d.fl = __double2float_rn(fl - (double)d.fh);
     // rows at t = 0 evaluated at u_0 = g
     double hinf = 0.0;
     if (g.rows & SL_MASS) hinf = nan_max(hinf, fabs(g.dx * s1 - d.M));
@@ -88,6 +95,42 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
     }
     d.h0_inf = hinf;
     sd[warp] = d;
+  }
+  if (ic_u) {
+    // IC block of this sample (slice k = 0, u0 = u_hat): the rows u_i - g_i are linear and
+    // independent per variable, so one Newton step from (u_hat, 0) lands on u = g,
+    // lambda = u_hat - g (no step when u_hat already satisfies them to tol_kkt)
+    const double *row = ic_uh + (size_t)warp * g.n_vars;
+    double mx = 0.0, sq = 0.0;
+    for (int i = lane; i < g.nx; i += 32) {
+      const double dv = row[i] - pg[i];
+      sq = fma(dv, dv, sq);
+      mx = nan_max(mx, fabs(dv));
+    }
+    mx = warp_max(mx);
+    sq = warp_sum(sq);
+    const bool take = !(mx <= tol_kkt);
+    double *out = ic_u + (size_t)warp * g.n_vars;
+    double *lb = ic_lam + (size_t)warp * g.n_rows;
+    for (int i = lane; i < g.nx; i += 32) {
+      out[i] = take ? pg[i] : row[i];
+      lb[i] = take ? row[i] - pg[i] : 0.0;
+    }
+    if (lane == 0) {
+      if (g.off_mass >= 0) lb[g.off_mass] = 0.0;
+      if (g.off_energy >= 0) lb[g.off_energy] = 0.0;
+      if (g.off_bound >= 0) lb[g.off_bound] = 0.0;
+      BlockStat st;
+      st.iters = take ? 1 : 0;
+      st.backtracks = 0;
+      st.corrections = 0;
+      st.status = (mx == mx && !isinf(mx)) ? SNAP_SAMPLE_OK : SNAP_SAMPLE_NONFINITE;
+      st.kkt_inf = take ? 0.0 : mx;
+      // rows at t = 0 implied by the IC rows, evaluated at u_0 = g (computed above)
+      st.h_inf = nan_max(take ? 0.0 : mx, sd[warp].h0_inf);
+      st.obj = take ? 0.5 * sq : 0.0;
+      ic_bst[(size_t)warp * g.nt] = st;
+    }
   }
 }
 
@@ -780,9 +823,11 @@ k1d_backward(Geom1D g, int B, const double *__restrict__ gu, const double *__res
       w = sf.w; wb = sf.wb;
       f.d0 = sf.d0; f.d1 = sf.d1; f.d2 = sf.d2;
       f.l10 = sf.l10; f.l20 = sf.l20; f.l21 = sf.l21;
+      f.i0 = 1.0 / f.d0; f.i1 = 1.0 / f.d1; f.i2 = 1.0 / f.d2;
     } else if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-      f.d0 = f.d1 = f.d2 = 0.0;   // singular: the division below yields Inf/NaN
+      f.d0 = f.d1 = f.d2 = 0.0;   // singular: the reciprocals below are Inf -> NaN gradients
       f.l10 = f.l20 = f.l21 = 0.0;
+      f.i0 = f.i1 = f.i2 = 1.0 / 0.0;
     }
     double bm, be, bb;
     ldl3_solve(f, v0, v1, v2, bm, be, bb);
@@ -927,9 +972,11 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
   int launches = 0;
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd);
+  const bool mixed = path == SNAP_PATH_MIXED;
+  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, u_hat, mixed ? u : nullptr,
+                                             lambda, w.bst, o.tol_kkt);
   launches++;
-  if (path == SNAP_PATH_MIXED) {
+  if (mixed) {
     const int pid = snap_prof_begin(s, "k1d_mixed");
     launch_1d_mixed(g, B, u_hat, params, w.sd, u, lambda, w.bst, (SliceFactor *)cache, o, 0, s);
     snap_prof_end(s, pid);
@@ -961,7 +1008,8 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
                                cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd);
+  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
+                                             nullptr, 0.0);
   SNAP_DISPATCH_NPL(g.nx, launch_residual, g, B, u, params, w.sd, h, w.smax, s);
   int launches = 2;
   if (h_inf) {
@@ -978,7 +1026,8 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
                                double *grad_params, void *ws, cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd);
+  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
+                                             nullptr, 0.0);
   const int pid = snap_prof_begin(s, "k1d_backward");
   SNAP_DISPATCH_NPL(g.nx, launch_backward, g, B, grad_u, u, lambda, params, stats, w.sd,
                     (const SliceFactor *)cache, grad_u_hat, grad_params, w.contrib, s);

@@ -17,6 +17,9 @@
 //            double-float;
 //   phase 3  (4 lanes per slice): u = fma(a, u_hat, c) in FP64, 16-byte stores.
 //
+// The IC slices (k = 0) are solved by the per-sample prepare kernel (k1d_params), a full
+// warp per slice, and skipped here.
+//
 // A slice whose values leave the range of the float-pair representation (|u_hat| outside
 // [2^-74, 2^57], or non-finite) falls back to FP64 moments and the FP64 iteration.
 #include <cuda_runtime.h>
@@ -30,7 +33,7 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 
-enum { KIND_MOMENT = 0, KIND_IC_G = 1, KIND_IC_KEEP = 2, KIND_NONE = 3 };
+enum { KIND_MOMENT = 0, KIND_NONE = 3 };
 
 __device__ __forceinline__ double nan_max(double a, double b) { return (a < b || b != b) ? b : a; }
 
@@ -61,66 +64,80 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
   const long long ntiles = (total + 31) >> 5;
   const int wpb = blockDim.x >> 5;
   const int nx = g.nx, ih = g.ih;
+  const SliceOptsT<float> so_f = slice_opts<float>(o, o.tol_kkt);
+  const SliceOptsT<df64> so_d = slice_opts<df64>(o, o.tol_kkt);
+  const df64 dxd(g.dx);
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb) {
     const long long sbase = tile << 5;
     // ---------------- phase 1 ----------------
+    {
+      // pull the tile (32 consecutive slices, contiguous in HBM) into L2 ahead of the loads
+      const long long s_end = (sbase + 32 < total) ? sbase + 32 : total;
+      const char *t0 = reinterpret_cast<const char *>(uh + (size_t)sbase * nx);
+      const size_t bytes = (size_t)(s_end - sbase) * nx * sizeof(double);
+      for (size_t off = (size_t)lane * 128; off < bytes; off += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(t0 + off));
+    }
     df64 m1(0.0f, 0.0f), m2(0.0f, 0.0f);
     float mmx = -INFINITY, mmn = INFINITY;
     int mok = 1;
-    double ic_max = 0.0, ic_sq = 0.0;
 #pragma unroll 1
     for (int rho = 0; rho < 4; ++rho) {
       const long long s = sbase + 8 * rho + q;
       float s1h = 0.0f, s1e = 0.0f, s2h = 0.0f, s2e = 0.0f;
       float pmx = -INFINITY, pmn = INFINITY;
       int ok = 1;
-      double dmax = 0.0, dsq = 0.0;
       if (s < total) {
         const int k = (int)(s % g.nt);
         const double *row = uh + (size_t)s * nx;
         if (k == 0) {
-          const double *pg = params + (size_t)(s / g.nt) * g.n_params;
-          for (int i = 2 * r; i < nx; i += 8) {
-            const double2 v = *reinterpret_cast<const double2 *>(row + i);
-            const double d0 = v.x - pg[i], d1 = v.y - pg[i + 1];
-            dsq = fma(d0, d0, dsq);
-            dsq = fma(d1, d1, dsq);
-            dmax = nan_max(dmax, nan_max(fabs(d0), fabs(d1)));
-          }
+          // the IC slice is handled by the per-sample prepare kernel
         } else {
-          for (int i = 2 * r; i < nx; i += 8) {
-            const double2 v = *reinterpret_cast<const double2 *>(row + i);
-            float h0, l0, h1, l1;
-            ok &= df_split(v.x, h0, l0);
-            ok &= df_split(v.y, h1, l1);
-            if (i == 0 || i == ih) { h0 = 0.0f; l0 = 0.0f; }
-            if (i + 1 == ih) { h1 = 0.0f; l1 = 0.0f; }
-            else { pmx = fmaxf(pmx, h1); pmn = fminf(pmn, h1); }
-            if (i != 0 && i != ih) { pmx = fmaxf(pmx, h0); pmn = fminf(pmn, h0); }
-            // S1 += h + l (TwoSum on the leading parts, errors accumulated in s1e)
-            {
-              float t = s1h + h0, bb = t - s1h;
-              s1e += ((s1h - (t - bb)) + (h0 - bb)) + l0;
-              s1h = t;
-              t = s1h + h1; bb = t - s1h;
-              s1e += ((s1h - (t - bb)) + (h1 - bb)) + l1;
-              s1h = t;
+          // CH independent 16-byte loads in flight per lane, then the accumulation
+          constexpr int CH = 8;
+          for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
+            double2 v[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const int i = i0 + 8 * c;
+              v[c] = (i < nx) ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
             }
-            // S2 += (h + l)^2 = h^2 (TwoProd) + 2 h l (+ l^2, below 2^-48 relative)
-            {
-              float p = h0 * h0;
-              float pe = fmaf(h0, h0, -p);
-              pe = fmaf(h0 + h0, l0, pe);
-              float t = s2h + p, bb = t - s2h;
-              s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
-              s2h = t;
-              p = h1 * h1;
-              pe = fmaf(h1, h1, -p);
-              pe = fmaf(h1 + h1, l1, pe);
-              t = s2h + p; bb = t - s2h;
-              s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
-              s2h = t;
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+              const int i = i0 + 8 * c;
+              if (i >= nx) break;
+              float h0, l0, h1, l1;
+              ok &= df_split(v[c].x, h0, l0);
+              ok &= df_split(v[c].y, h1, l1);
+              if (i == 0 || i == ih) { h0 = 0.0f; l0 = 0.0f; }
+              if (i + 1 == ih) { h1 = 0.0f; l1 = 0.0f; }
+              else { pmx = fmaxf(pmx, h1); pmn = fminf(pmn, h1); }
+              if (i != 0 && i != ih) { pmx = fmaxf(pmx, h0); pmn = fminf(pmn, h0); }
+              // S1 += h + l (TwoSum on the leading parts, errors accumulated in s1e)
+              {
+                float t = s1h + h0, bb = t - s1h;
+                s1e += ((s1h - (t - bb)) + (h0 - bb)) + l0;
+                s1h = t;
+                t = s1h + h1; bb = t - s1h;
+                s1e += ((s1h - (t - bb)) + (h1 - bb)) + l1;
+                s1h = t;
+              }
+              // S2 += (h + l)^2 = h^2 (TwoProd) + 2 h l (+ l^2, below 2^-48 relative)
+              {
+                float p = h0 * h0;
+                float pe = fmaf(h0, h0, -p);
+                pe = fmaf(h0 + h0, l0, pe);
+                float t = s2h + p, bb = t - s2h;
+                s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
+                s2h = t;
+                p = h1 * h1;
+                pe = fmaf(h1, h1, -p);
+                pe = fmaf(h1 + h1, l1, pe);
+                t = s2h + p; bb = t - s2h;
+                s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
+                s2h = t;
+              }
             }
           }
         }
@@ -134,12 +151,9 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
         pmx = fmaxf(pmx, __shfl_xor_sync(FULL, pmx, off));
         pmn = fminf(pmn, __shfl_xor_sync(FULL, pmn, off));
         ok &= __shfl_xor_sync(FULL, ok, off);
-        dmax = nan_max(dmax, __shfl_xor_sync(FULL, dmax, off));
-        dsq += __shfl_xor_sync(FULL, dsq, off);
       }
       if (r == rho) {
         m1 = a1; m2 = a2; mmx = pmx; mmn = pmn; mok = ok;
-        ic_max = dmax; ic_sq = dsq;
       }
     }
     // ---------------- phase 2: one slice per lane ----------------
@@ -155,18 +169,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
       const SampleDerived dv = sd[b];
       BlockStat st;
       if (k == 0) {
-        const bool take = !(ic_max <= o.tol_kkt);
-        kind = take ? KIND_IC_G : KIND_IC_KEEP;
-        st.iters = take ? 1 : 0;
-        st.backtracks = 0;
-        st.corrections = 0;
-        st.status = (ic_max == ic_max && !isinf(ic_max)) ? SNAP_SAMPLE_OK : SNAP_SAMPLE_NONFINITE;
-        st.kkt_inf = take ? 0.0 : ic_max;
-        st.h_inf = nan_max(take ? 0.0 : ic_max, dv.h0_inf);
-        st.obj = take ? 0.5 * ic_sq : 0.0;
-        if (g.off_mass >= 0) lb[g.off_mass] = 0.0;
-        if (g.off_energy >= 0) lb[g.off_energy] = 0.0;
-        if (g.off_bound >= 0) lb[g.off_bound] = 0.0;
+        // IC slice: written by the prepare kernel
       } else {
         kind = KIND_MOMENT;
         const double uh0 = row[0], uhh = row[ih];
@@ -174,43 +177,58 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
         double hm, he, hb, res, S1d, S2d;
         SliceResult R;
         double lmd, led, lbd;
-        const bool range_ok = mok && isfinite(uh0) && isfinite(uhh) && fabs(uh0) < 1.4e17 &&
-                              fabs(uhh) < 1.4e17;
+        float u0h, u0l, uhh_h, uhh_l, ch, cl;
+        const bool range_ok = mok && df_split(uh0, u0h, u0l) && df_split(uhh, uhh_h, uhh_l) &&
+                              df_split(C, ch, cl);
         if (range_ok) {
           SliceIn<df64> d;
           d.S1 = m1; d.S2 = m2;
           d.mx = df64(mmx, 0.0f); d.mn = df64(mmn, 0.0f);
-          d.uh0 = df64(uh0); d.uhh = df64(uhh);
+          d.uh0 = df64(u0h, u0l); d.uhh = df64(uhh_h, uhh_l);
           d.n = df64((float)(nx - 2), 0.0f);
           d.nint = nx - 2;
-          d.dx = df64(g.dx);
-          d.M = df64(dv.M);
+          d.dx = dxd;
+          d.M = df64(dv.Mh, dv.Ml);
           df64 E(0.0f, 0.0f);
           if (g.rows & SL_ENERGY) {
-            const df64 e = df64(dv.E0) * df_pow(df64(dv.q), k);
-            const df64 fl = df64(dv.M * dv.M + g.energy_floor);
+            const df64 e = df64(dv.E0h, dv.E0l) * df_pow(df64(dv.qh, dv.ql), k);
+            const df64 fl = df64(dv.fh, dv.fl);
             E = (e >= fl) ? e : fl;
           }
           d.E = E;
-          d.C = df64(C);
+          d.C = df64(ch, cl);
           d.rows = g.rows;
-          const bool infeasible = ((g.rows & SL_BOUND) && C < 0.0) ||
-                                  ((g.rows & SL_ENERGY) && (double)E < ((g.rows & SL_MASS) ? dv.M * dv.M : 0.0));
-          SliceZ<df64> z{df64(1.0f, 0.0f), df64(0.0f, 0.0f), d.uh0, d.uhh, df64(0.0f, 0.0f),
-                         df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
+          const df64 zero(0.0f, 0.0f);
+          const bool infeasible = ((g.rows & SL_BOUND) && ch < 0.0f) ||
+                                  ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? d.M * d.M : zero));
+          SliceZ<df64> z{df64(1.0f, 0.0f), zero, d.uh0, d.uhh, zero, zero, zero};
           SliceEval<df64> e;
           if (infeasible) {
             slice_eval(d, z, e);
             R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
           } else {
-            R = slice_solve_mixed(d, z, e, o);
+            R = slice_solve_mixed(d, z, e, o, so_f, so_d);
           }
           A = (double)z.a; Cc = (double)z.c; P0 = (double)z.p0; PH = (double)z.ph;
           lmd = (double)z.lm; led = (double)z.le; lbd = (double)z.lb;
-          hm = (double)e.hm; he = (double)e.he; hb = (double)e.hb; res = (double)e.res;
-          S1d = (double)m1; S2d = (double)m2;
+          // statistics in double-float, one conversion each
+          const df64 hmx = sl_max(sl_max(sl_abs(e.hm), sl_abs(e.he)), sl_abs(e.hb));
+          const df64 am1 = z.a - df64(1.0f, 0.0f);
+          const df64 d0 = z.p0 - d.uh0, dh = z.ph - d.uhh;
+          const df64 obj = (am1 * am1 * d.S2 + df64(2.0f, 0.0f) * am1 * z.c * d.S1 + z.c * z.c * d.n +
+                            d0 * d0 + dh * dh) * df64(0.5f, 0.0f);
+          st.iters = R.iters;
+          st.backtracks = R.backtracks;
+          st.status = R.status;
+          st.corrections = R.corrections;
+          st.kkt_inf = (double)e.res;
+          st.h_inf = (double)hmx;
+          st.obj = (double)obj;
+          if (e.res != e.res) st.kkt_inf = NAN;
+          if (hmx != hmx) st.h_inf = NAN;
           if (cache) {
             const double al = (double)e.alpha, be = (double)e.beta;
+            S1d = (double)m1; S2d = (double)m2;
             SliceIn<double> d64 = slice_in_cast<double>(d);
             SliceZ<double> z64{A, Cc, P0, PH, lmd, led, lbd};
             double s00, s01, s02, s11, s12, s22;
@@ -279,27 +297,29 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
             cache[s] = sf;
           }
         }
-        st.iters = R.iters;
-        st.backtracks = R.backtracks;
-        st.status = R.status;
-        st.corrections = R.corrections;
-        st.kkt_inf = res;
-        st.h_inf = nan_max(nan_max(fabs(hm), fabs(he)), fabs(hb));
-        const double am1 = A - 1.0;
-        st.obj = 0.5 * (am1 * am1 * S2d + 2.0 * am1 * Cc * S1d + Cc * Cc * (double)(nx - 2) +
-                        (P0 - uh0) * (P0 - uh0) + (PH - uhh) * (PH - uhh));
+        if (!range_ok) {
+          st.iters = R.iters;
+          st.backtracks = R.backtracks;
+          st.status = R.status;
+          st.corrections = R.corrections;
+          st.kkt_inf = res;
+          st.h_inf = nan_max(nan_max(fabs(hm), fabs(he)), fabs(hb));
+          const double am1 = A - 1.0;
+          st.obj = 0.5 * (am1 * am1 * S2d + 2.0 * am1 * Cc * S1d + Cc * Cc * (double)(nx - 2) +
+                          (P0 - uh0) * (P0 - uh0) + (PH - uhh) * (PH - uhh));
+        }
         if (g.off_mass >= 0) lb[g.off_mass + k] = lmd;
         if (g.off_energy >= 0) lb[g.off_energy + k] = led;
         if (g.off_bound >= 0) lb[g.off_bound + k] = lbd;
+        bst[s] = st;
       }
-      bst[s] = st;
     }
     // ---------------- phase 3: write-back, 4 lanes per slice ----------------
 #pragma unroll 1
     for (int rho = 0; rho < 4; ++rho) {
       const int src = 4 * q + rho;
       const double a = __shfl_sync(FULL, A, src);
-      const double c = __shfl_sync(FULL, Cc, src);
+      const double c0 = __shfl_sync(FULL, Cc, src);
       const double p0 = __shfl_sync(FULL, P0, src);
       const double ph = __shfl_sync(FULL, PH, src);
       const int kd = __shfl_sync(FULL, kind, src);
@@ -308,27 +328,23 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
       const double *row = uh + (size_t)s2 * nx;
       double *out = u + (size_t)s2 * nx;
       if (kd == KIND_MOMENT) {
-        for (int i = 2 * r; i < nx; i += 8) {
-          const double2 v = *reinterpret_cast<const double2 *>(row + i);
-          double2 w;
-          w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v.x, c));
-          w.y = (i + 1 == ih) ? ph : fma(a, v.y, c);
-          *reinterpret_cast<double2 *>(out + i) = w;
-        }
-      } else {
-        const int b = (int)(s2 / g.nt);
-        const double *pg = params + (size_t)b * g.n_params;
-        double *lb = lam + (size_t)b * g.n_rows;
-        const bool take = kd == KIND_IC_G;
-        for (int i = 2 * r; i < nx; i += 8) {
-          const double2 v = *reinterpret_cast<const double2 *>(row + i);
-          const double g0 = pg[i], g1 = pg[i + 1];
-          double2 w;
-          w.x = take ? g0 : v.x;
-          w.y = take ? g1 : v.y;
-          *reinterpret_cast<double2 *>(out + i) = w;
-          lb[i] = take ? v.x - g0 : 0.0;
-          lb[i + 1] = take ? v.y - g1 : 0.0;
+        constexpr int CH = 8;
+        for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
+          double2 v[CH];
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int i = i0 + 8 * c;
+            v[c] = (i < nx) ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
+          }
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            const int i = i0 + 8 * c;
+            if (i >= nx) break;
+            double2 w;
+            w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v[c].x, c0));
+            w.y = (i + 1 == ih) ? ph : fma(a, v[c].y, c0);
+            *reinterpret_cast<double2 *>(out + i) = w;
+          }
         }
       }
     }

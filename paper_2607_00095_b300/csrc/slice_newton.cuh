@@ -65,6 +65,12 @@ struct SliceOptsT {
 template <class T>
 DF_INL T sl_abs(T x) { return x < T(0) ? -x : x; }
 
+// 1/x: exact division in FP64, the IEEE-rounded reciprocal in float, the double-float
+// quotient in df64
+DF_INL double sl_rcp(double x) { return 1.0 / x; }
+DF_INL float sl_rcp(float x) { return df_rcp(x); }
+DF_INL df64 sl_rcp(df64 x) { return df64(1.0f, 0.0f) / x; }
+
 template <class T>
 DF_INL T sl_max(T x, T y) { return (x < y) ? y : x; }
 
@@ -131,36 +137,39 @@ DF_INL void slice_eval(const SliceIn<T> &d, const SliceZ<T> &z,
   e.res = r;
 }
 
-// 3x3 symmetric LDL^T without pivoting; returns false on a zero pivot.
+// 3x3 symmetric LDL^T without pivoting; returns false on a zero pivot.  The reciprocals of
+// the pivots are kept for the solve.
 template <class T>
 struct Ldl3 {
-  T d0, d1, d2, l10, l20, l21;
+  T d0, d1, d2, l10, l20, l21, i0, i1, i2;
 };
 
 template <class T>
-DF_INL bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T s22,
-                                            Ldl3<T> &f) {
+DF_INL bool ldl3_factor(T s00, T s01, T s02, T s11, T s12, T s22, Ldl3<T> &f) {
   f.d0 = s00;
   if (f.d0 == T(0)) return false;
-  f.l10 = s01 / f.d0;
-  f.l20 = s02 / f.d0;
+  f.i0 = sl_rcp(f.d0);
+  f.l10 = s01 * f.i0;
+  f.l20 = s02 * f.i0;
   f.d1 = s11 - f.l10 * s01;
   if (f.d1 == T(0)) return false;
-  f.l21 = (s12 - f.l20 * s01) / f.d1;
-  f.d2 = s22 - f.l20 * s02 - f.l21 * (s12 - f.l20 * s01);
+  f.i1 = sl_rcp(f.d1);
+  const T t12 = s12 - f.l20 * s01;
+  f.l21 = t12 * f.i1;
+  f.d2 = s22 - f.l20 * s02 - f.l21 * t12;
   if (f.d2 == T(0)) return false;
+  f.i2 = sl_rcp(f.d2);
   return true;
 }
 
 template <class T>
-DF_INL void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T &x0, T &x1,
-                                           T &x2) {
+DF_INL void ldl3_solve(const Ldl3<T> &f, T r0, T r1, T r2, T &x0, T &x1, T &x2) {
   const T y0 = r0;
   const T y1 = r1 - f.l10 * y0;
   const T y2 = r2 - f.l20 * y0 - f.l21 * y1;
-  x2 = y2 / f.d2;
-  x1 = y1 / f.d1 - f.l21 * x2;
-  x0 = y0 / f.d0 - f.l10 * x1 - f.l20 * x2;
+  x2 = y2 * f.i2;
+  x1 = y1 * f.i1 - f.l21 * x2;
+  x0 = y0 * f.i0 - f.l10 * x1 - f.l20 * x2;
 }
 
 // Schur complement S = J W^-1 J^T of the slice rows at z with W diagonal (w interior, wb at
@@ -205,7 +214,7 @@ DF_INL bool slice_sosc(const SliceIn<T> &d, const SliceZ<T> &z, const SliceEval<
                         ((d.rows & SL_BOUND) != 0);
   if (e.alpha == T(0) || e.beta == T(0)) return false;
   T s00, s01, s02, s11, s12, s22;
-  slice_schur(d, z, e.su, e.su2, T(1) / e.alpha, T(1) / e.beta, s00, s01, s02, s11, s12, s22);
+  slice_schur(d, z, e.su, e.su2, sl_rcp(e.alpha), sl_rcp(e.beta), s00, s01, s02, s11, s12, s22);
   Ldl3<T> f;
   return ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
          slice_inertia_ok(f, e.alpha, e.beta, d.nint, m_present, 3 - m_present);
@@ -242,8 +251,8 @@ DF_INL bool slice_direction(const SliceIn<L> &d, const SliceZ<L> &z, const Slice
   for (int corr = 0; corr <= max_corrections; ++corr) {
     const L w = e.alpha + delta, wb = e.beta + delta;
     if (!(w == L(0)) && !(wb == L(0))) {
-      iw = L(1) / w;
-      iwb = L(1) / wb;
+      iw = sl_rcp(w);
+      iwb = sl_rcp(wb);
       L s00, s01, s02, s11, s12, s22;
       slice_schur(d, z, e.su, e.su2, iw, iwb, s00, s01, s02, s11, s12, s22);
       if (ldl3_factor(s00, s01, s02, s11, s12, s22, f) &&
@@ -307,11 +316,11 @@ DF_INL void slice_newton_phase(const SliceIn<T> &d, const SliceIn<L> &dl, SliceZ
       const L da = L(2) * dl.dx * dzl.le;
       const L db = da + L(2) * dzl.lb;
       if (el.alpha > L(0) && da < L(0)) {
-        const L tm = sl.w_keep1 * el.alpha / (-da);
+        const L tm = sl.w_keep1 * el.alpha * sl_rcp(-da);
         if (tm < tl) tl = tm;
       }
       if (el.beta > L(0) && db < L(0)) {
-        const L tm = sl.w_keep1 * el.beta / (-db);
+        const L tm = sl.w_keep1 * el.beta * sl_rcp(-db);
         if (tm < tl) tl = tm;
       }
     }
@@ -374,10 +383,11 @@ DF_INL df64 df_from_float(float x) { return df64(x, 0.0f); }
 // (iterative refinement of the Newton step), to o.tol_kkt.  The float phase stops when ||F||_inf <= max(1e-5 ||F(z0)||_inf, 1e-6 * scale)
 // (scale = the largest magnitude among the slice data; float rounding puts a floor near
 // 1e-7 * scale under ||F||), when a line search needs more than 8 halvings (the float merit
-// is then at its rounding floor), or after half of the iteration budget.  dd holds the
+// is then at its rounding floor), or when only 8 steps of the iteration budget are left.  dd holds the
 // inputs in df64; the result z is returned in df64.
 DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
-                                     SliceEval<df64> &e, const SolverOpts &o) {
+                                     SliceEval<df64> &e, const SolverOpts &o,
+                                     const SliceOptsT<float> &sf, const SliceOptsT<df64> &sd) {
   SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
   SliceIn<float> d32;
   d32.S1 = dd.S1.hi; d32.S2 = dd.S2.hi; d32.mx = dd.mx.hi; d32.mn = dd.mn.hi;
@@ -389,13 +399,14 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
   SliceEval<float> e32;
   slice_eval(d32, z32, e32);
   if (sl_finite(e32.res)) {
-    SliceOptsT<float> s32 = slice_opts<float>(o, o.tol_kkt);
+    SliceOptsT<float> s32 = sf;
     s32.max_backtracks = o.max_backtracks < 8 ? o.max_backtracks : 8;
     float scale = fmaxf(fmaxf(fabsf(d32.mx), fabsf(d32.mn)), fmaxf(fabsf(d32.uh0), fabsf(d32.uhh)));
     scale = fmaxf(scale, fmaxf(fabsf(d32.M), sqrtf(fabsf(d32.E) + fabsf(d32.C))));
     float tol32 = fmaxf(1e-5f * e32.res, 1e-6f * scale);
     if (tol32 > s32.tol) s32.tol = tol32;
-    slice_newton_phase<float, float>(d32, d32, z32, e32, s32, s32, o.max_iter / 2, R);
+    const int budget32 = o.max_iter > 16 ? o.max_iter - 8 : o.max_iter / 2;
+    slice_newton_phase<float, float>(d32, d32, z32, e32, s32, s32, budget32, R);
     if (R.status != SNAP_SAMPLE_NONFINITE) {
       z.a = df_from_float(z32.a); z.c = df_from_float(z32.c);
       z.p0 = df_from_float(z32.p0); z.ph = df_from_float(z32.ph);
@@ -403,8 +414,6 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
     }
   }
   R.status = SNAP_SAMPLE_OK;
-  const SliceOptsT<df64> sd = slice_opts<df64>(o, o.tol_kkt);
-  const SliceOptsT<float> sf = slice_opts<float>(o, o.tol_kkt);
   slice_eval(dd, z, e);
   slice_newton_phase<df64, float>(dd, d32, z, e, sd, sf, o.max_iter - R.iters, R);
   if (R.status == SNAP_SAMPLE_OK) {

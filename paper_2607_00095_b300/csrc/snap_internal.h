@@ -58,6 +58,8 @@ struct Geom1D {
 //   double[B*nt]      per-slice residual maxima
 struct SampleDerived {
   double M, E0, h0_inf, q;   // q = exp(-r dt): E0 exp(-r t_k) = E0 q^k
+  // the same values as float pairs (hi, lo) for the double-float path; f = M^2 + floor
+  float Mh, Ml, E0h, E0l, qh, ql, fh, fl;
 };
 
 // Per-slice contributions of the backward pass to dL/dtheta (summed per sample):

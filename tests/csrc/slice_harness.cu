@@ -63,7 +63,7 @@ extern "C" int harness_slice(int mode, const double *in, int rows, int nint, con
     SliceZ<df64> z{df64(1.0f, 0.0f), df64(0.0f, 0.0f), d.uh0, d.uhh, df64(0.0f, 0.0f),
                    df64(0.0f, 0.0f), df64(0.0f, 0.0f)};
     SliceEval<df64> e;
-    SliceResult R = slice_solve_mixed(d, z, e, o);
+    SliceResult R = slice_solve_mixed(d, z, e, o, slice_opts<float>(o, o.tol_kkt), slice_opts<df64>(o, o.tol_kkt));
     put(z, e, R, oz, os, ores);
   }
   return 0;
