@@ -286,10 +286,13 @@ SNAP_API snap_status snap_batch_project_grouped(snap_batch_t b, const snap_optio
  * kernel; used to state the arithmetic roofline.  Host call, synchronous. */
 SNAP_API snap_status snap_measure_fp64_rate(int device, double *fma_per_s);
 
-/* Per-kernel timing: when enabled, every kernel launch of the library outside stream capture
- * is bracketed by two CUDA events recorded on its stream.  snap_profile_read waits for the
- * recorded events of kernel `name` (e.g. "k1d_moment") and returns their summed elapsed time
- * and count; snap_profile_reset drops all records.  Host calls. */
+/* Per-kernel timing: when enabled (on = 1), every kernel launch of the library outside stream
+ * capture is bracketed by two CUDA events recorded on its stream; with on = 2 the events are
+ * also recorded into graphs being captured (as event nodes: after a replay they hold that
+ * replay's times).  snap_profile_read waits for the recorded events of kernel `name` (e.g.
+ * "k1d_mixed") and returns their summed elapsed time and count; snap_profile_reset drops all
+ * records (call it only when no captured graph that records them will be replayed again).
+ * Host calls. */
 SNAP_API snap_status snap_profile_enable(int on);
 SNAP_API snap_status snap_profile_reset(void);
 SNAP_API snap_status snap_profile_read(const char *name, double *total_ms, long long *launches);

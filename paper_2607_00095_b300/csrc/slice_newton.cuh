@@ -137,6 +137,36 @@ DF_INL void slice_eval(const SliceIn<T> &d, const SliceZ<T> &z,
   e.res = r;
 }
 
+// df64 evaluation: the residual components, which cancel as the iteration converges, are
+// formed in df64; the merit phi (compared by the Armijo test against a factor 1 - 2 c1 t,
+// far above float rounding) and ||F||_inf are then formed from their float images.
+DF_INL void slice_eval(const SliceIn<df64> &d, const SliceZ<df64> &z, SliceEval<df64> &e) {
+  const df64 two(2.0f, 0.0f), one(1.0f, 0.0f);
+  e.alpha = one + two * d.dx * z.le;
+  e.beta = e.alpha + two * z.lb;
+  e.P = e.alpha * z.a - one;
+  e.Q = e.alpha * z.c + d.dx * z.lm;
+  e.su = z.a * d.S1 + z.c * d.n;
+  e.su2 = z.a * z.a * d.S2 + two * z.a * z.c * d.S1 + z.c * z.c * d.n;
+  e.g0 = e.beta * z.p0 - d.uh0 + d.dx * z.lm;
+  e.gh = e.beta * z.ph - d.uhh + d.dx * z.lm;
+  const df64 pp = z.p0 * z.p0 + z.ph * z.ph;
+  const df64 zero(0.0f, 0.0f);
+  e.hm = (d.rows & SL_MASS) ? d.dx * (e.su + z.p0 + z.ph) - d.M : zero;
+  e.he = (d.rows & SL_ENERGY) ? d.dx * (e.su2 + pp) - d.E : zero;
+  e.hb = (d.rows & SL_BOUND) ? pp - d.C : zero;
+  const float P = e.P.hi, Q = e.Q.hi, g0 = e.g0.hi, gh = e.gh.hi;
+  const float hm = e.hm.hi, he = e.he.hi, hb = e.hb.hi;
+  float gi2 = P * P * d.S2.hi + 2.0f * P * Q * d.S1.hi + Q * Q * d.n.hi;
+  if (gi2 < 0.0f) gi2 = 0.0f;
+  const float phi = 0.5f * (gi2 + g0 * g0 + gh * gh + hm * hm + he * he + hb * hb);
+  float r = fmaxf(fabsf(P * d.mx.hi + Q), fabsf(P * d.mn.hi + Q));
+  r = fmaxf(r, fmaxf(fmaxf(fabsf(g0), fabsf(gh)), fmaxf(fmaxf(fabsf(hm), fabsf(he)), fabsf(hb))));
+  if (phi != phi) r = phi;
+  e.phi = df64(phi, 0.0f);
+  e.res = df64(r, 0.0f);
+}
+
 // 3x3 symmetric LDL^T without pivoting; returns false on a zero pivot.  The reciprocals of
 // the pivots are kept for the solve.
 template <class T>

@@ -1,5 +1,7 @@
 // Optional per-kernel timing with CUDA events recorded on the launching stream around each
-// kernel.  Off by default; never active while the stream is being captured into a graph.
+// kernel.  Off by default.  Mode 1 skips launches that are being captured into a graph;
+// mode 2 records the events into the graph as event nodes, so that after a replay the
+// recorded pairs hold that replay's kernel durations.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -18,6 +20,7 @@ struct Rec {
 
 std::mutex g_mu;
 bool g_on = false;
+bool g_in_graph = false;   // also record (as graph event nodes) while a stream is captured
 std::vector<Rec> g_recs;
 
 bool capturing(cudaStream_t s) {
@@ -30,7 +33,7 @@ bool capturing(cudaStream_t s) {
 
 int snap_prof_begin(cudaStream_t s, const char *name) {
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_on || capturing(s)) return -1;
+  if (!g_on || (capturing(s) && !g_in_graph)) return -1;
   Rec r;
   r.name = name;
   if (cudaEventCreate(&r.a) != cudaSuccess) return -1;
@@ -51,6 +54,7 @@ extern "C" {
 SNAP_API snap_status snap_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_mu);
   g_on = on != 0;
+  g_in_graph = on == 2;
   return SNAP_OK;
 }
 
