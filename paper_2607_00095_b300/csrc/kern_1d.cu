@@ -59,7 +59,9 @@ __device__ __forceinline__ double energy_target(const Geom1D &g, const SampleDer
 __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
                            SampleDerived *__restrict__ sd, const double *__restrict__ ic_uh,
                            double *__restrict__ ic_u, double *__restrict__ ic_lam,
-                           BlockStat *__restrict__ ic_bst, double tol_kkt) {
+                           BlockStat *__restrict__ ic_bst, double tol_kkt,
+                           double *__restrict__ bwd_gh, BwdContrib *__restrict__ bwd_contrib,
+                           double *__restrict__ bwd_gp, const snap_stats *__restrict__ bwd_st) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= B) return;
@@ -130,6 +132,16 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
       st.h_inf = nan_max(take ? 0.0 : mx, sd[warp].h0_inf);
       st.obj = take ? 0.5 * sq : 0.0;
       ic_bst[(size_t)warp * g.nt] = st;
+    }
+  }
+  if (bwd_gh) {
+    // adjoint on the IC block: K = [I I; I 0] -> a = 0 (b_IC = gbar enters dL/dg later)
+    const bool bad = bwd_st && bwd_st[warp].status != SNAP_SAMPLE_OK;
+    double *out = bwd_gh + (size_t)warp * g.n_vars;
+    for (int i = lane; i < g.nx; i += 32) out[i] = bad ? NAN : 0.0;
+    if (lane == 0) {
+      bwd_contrib[(size_t)warp * g.nt] = BwdContrib{0.0, 0.0, 0.0, 0.0};
+      if (bwd_gp && (g.rows & SL_BOUND)) bwd_gp[(size_t)warp * g.n_params + g.p_c] = bad ? NAN : 0.0;
     }
   }
 }
@@ -758,110 +770,6 @@ __global__ void k_rowmax(int B, int nblk, const double *__restrict__ smax,
   if (lane == 0) out[warp] = m;
 }
 
-// ---------------------------------------------------------------------------------------
-// Adjoint: K [a; b] = [gbar; 0] per slice with K at the solution; one warp per slice.
-// contrib[s] = (b_m, b_e e^{-r t} [exp branch], b_e [floor branch], -b_e t E0 e^{-r t}).
-// ---------------------------------------------------------------------------------------
-template <int NPL>
-__global__ void __launch_bounds__(128)
-k1d_backward(Geom1D g, int B, const double *__restrict__ gu, const double *__restrict__ u,
-             const double *__restrict__ lam, const double *__restrict__ params,
-             const snap_stats *__restrict__ fst, const SampleDerived *__restrict__ sd,
-             const SliceFactor *__restrict__ cache, double *__restrict__ gh,
-             double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
-  const int lane = threadIdx.x & 31;
-  const long long total = (long long)B * g.nt;
-  const int wpb = blockDim.x >> 5;
-  const int nx = g.nx;
-  for (long long s = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); s < total;
-       s += (long long)gridDim.x * wpb) {
-    const int b = (int)(s / g.nt);
-    const int k = (int)(s % g.nt);
-    const bool bad = fst && fst[b].status != SNAP_SAMPLE_OK;
-    double *out = gh + (size_t)s * nx;
-    if (k == 0) {
-      // IC block: K = [I I; I 0] -> a = 0, b_IC = gbar (used by the per-sample pass)
-      for (int i = lane; i < nx; i += 32) out[i] = bad ? NAN : 0.0;
-      if (lane == 0) {
-        contrib[s] = BwdContrib{0.0, 0.0, 0.0, 0.0};
-        if (gp && (g.rows & SL_BOUND)) gp[(size_t)b * g.n_params + g.p_c] = bad ? NAN : 0.0;
-      }
-      continue;
-    }
-    const double *row = u + (size_t)s * nx;
-    const double *grow = gu + (size_t)s * nx;
-    const double *pg = params + (size_t)b * g.n_params;
-    const double *lb = lam + (size_t)b * g.n_rows;
-    double U[NPL], Gb[NPL];
-#pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      const int i = lane + 32 * j;
-      U[j] = (i < nx) ? row[i] : 0.0;
-      Gb[j] = (i < nx) ? grow[i] : 0.0;
-    }
-    const double lme = (g.rows & SL_ENERGY) ? lb[g.off_energy + k] : 0.0;
-    const double lbb = (g.rows & SL_BOUND) ? lb[g.off_bound + k] : 0.0;
-    SliceIn<double> d;
-    d.dx = g.dx;
-    d.n = (double)(nx - 2);
-    d.nint = nx - 2;
-    d.rows = g.rows;
-    d.M = d.E = d.C = 0.0;
-    GenEval<NPL> e;
-    e.alpha = 1.0 + 2.0 * g.dx * lme;
-    e.beta = e.alpha + 2.0 * lbb;
-    e.p0 = bcast_elem<NPL>(U, 0, lane);
-    e.ph = bcast_elem<NPL>(U, g.ih, lane);
-    e.g0 = bcast_elem<NPL>(Gb, 0, lane);
-    e.gh = bcast_elem<NPL>(Gb, g.ih, lane);
-    double s00, s01, s02, s11, s12, s22, v0, v1, v2;
-    gen_schur<NPL>(g, d, U, Gb, e, e.alpha, e.beta, s00, s01, s02, s11, s12, s22, v0, v1, v2, lane);
-    Ldl3<double> f;
-    double w = e.alpha, wb = e.beta;
-    if (cache) {
-      const SliceFactor sf = cache[s];
-      w = sf.w; wb = sf.wb;
-      f.d0 = sf.d0; f.d1 = sf.d1; f.d2 = sf.d2;
-      f.l10 = sf.l10; f.l20 = sf.l20; f.l21 = sf.l21;
-      f.i0 = 1.0 / f.d0; f.i1 = 1.0 / f.d1; f.i2 = 1.0 / f.d2;
-    } else if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-      f.d0 = f.d1 = f.d2 = 0.0;   // singular: the reciprocals below are Inf -> NaN gradients
-      f.l10 = f.l20 = f.l21 = 0.0;
-      f.i0 = f.i1 = f.i2 = 1.0 / 0.0;
-    }
-    double bm, be, bb;
-    ldl3_solve(f, v0, v1, v2, bm, be, bb);
-    if (!(g.rows & SL_MASS)) bm = 0.0;
-    if (!(g.rows & SL_ENERGY)) be = 0.0;
-    if (!(g.rows & SL_BOUND)) bb = 0.0;
-#pragma unroll
-    for (int j = 0; j < NPL; ++j) {
-      const int i = lane + 32 * j;
-      if (i < nx) {
-        const bool bd = (i == 0 || i == g.ih);
-        const double a = (Gb[j] - g.dx * bm - 2.0 * g.dx * U[j] * be - (bd ? 2.0 * U[j] * bb : 0.0)) /
-                         (bd ? wb : w);
-        out[i] = bad ? NAN : a;
-      }
-    }
-    if (lane == 0) {
-      BwdContrib c{bm, 0.0, 0.0, 0.0};
-      if (g.rows & SL_ENERGY) {
-        const SampleDerived dv = sd[b];
-        const double r = pg[g.p_rate];
-        const double t = (double)k / (double)(g.nt - 1);
-        const double ex = exp(-r * t);
-        const bool expb = dv.E0 * ex >= dv.M * dv.M + g.energy_floor;
-        c.bex = expb ? be * ex : 0.0;
-        c.bfl = expb ? 0.0 : be;
-        c.br = expb ? -be * t * dv.E0 * ex : 0.0;
-      }
-      contrib[s] = c;
-      if (gp && (g.rows & SL_BOUND)) gp[(size_t)b * g.n_params + g.p_c + k] = bad ? NAN : bb;
-    }
-  }
-}
-
 // Per-sample part of dL/dtheta: g (through the IC rows, M and E0) and r.
 __global__ void k1d_backward_params(Geom1D g, int B, const double *__restrict__ gu,
                                     const double *__restrict__ params,
@@ -911,17 +819,6 @@ void launch_residual(const Geom1D &g, int B, const double *u, const double *para
   long long blocks = (total + 3) / 4;
   if (blocks > 148LL * 64) blocks = 148LL * 64;
   k1d_residual<NPL><<<(int)blocks, 128, 0, s>>>(g, B, u, params, sd, h, smax);
-}
-
-template <int NPL>
-void launch_backward(const Geom1D &g, int B, const double *gu, const double *u,
-                     const double *lam, const double *params, const snap_stats *fst,
-                     const SampleDerived *sd, const SliceFactor *cache, double *gh, double *gp,
-                     BwdContrib *contrib, cudaStream_t s) {
-  const long long total = (long long)B * g.nt;
-  long long blocks = (total + 3) / 4;
-  if (blocks > 148LL * 64) blocks = 148LL * 64;
-  k1d_backward<NPL><<<(int)blocks, 128, 0, s>>>(g, B, gu, u, lam, params, fst, sd, cache, gh, gp, contrib);
 }
 
 #define SNAP_DISPATCH_NPL(nx, FN, ...)                      \
@@ -974,7 +871,8 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   int launches = 0;
   const bool mixed = path == SNAP_PATH_MIXED;
   k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, u_hat, mixed ? u : nullptr,
-                                             lambda, w.bst, o.tol_kkt);
+                                             lambda, w.bst, o.tol_kkt, nullptr, nullptr, nullptr,
+                                             nullptr);
   launches++;
   if (mixed) {
     const int pid = snap_prof_begin(s, "k1d_mixed");
@@ -1009,7 +907,7 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
   k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
-                                             nullptr, 0.0);
+                                             nullptr, 0.0, nullptr, nullptr, nullptr, nullptr);
   SNAP_DISPATCH_NPL(g.nx, launch_residual, g, B, u, params, w.sd, h, w.smax, s);
   int launches = 2;
   if (h_inf) {
@@ -1027,10 +925,11 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
   k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
-                                             nullptr, 0.0);
-  const int pid = snap_prof_begin(s, "k1d_backward");
-  SNAP_DISPATCH_NPL(g.nx, launch_backward, g, B, grad_u, u, lambda, params, stats, w.sd,
-                    (const SliceFactor *)cache, grad_u_hat, grad_params, w.contrib, s);
+                                             nullptr, 0.0, grad_u_hat, w.contrib, grad_params,
+                                             stats);
+  const int pid = snap_prof_begin(s, "k1d_bwd_mixed");
+  launch_1d_bwd_mixed(g, B, grad_u, u, lambda, params, stats, w.sd, (const SliceFactor *)cache,
+                      grad_u_hat, grad_params, w.contrib, s);
   snap_prof_end(s, pid);
   int launches = 2;
   if (grad_params) {

@@ -107,6 +107,10 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
                                const double *params, double *h, double *h_inf, void *ws,
                                cudaStream_t s);
 size_t ws_bytes_1d(const snap_problem *p, int B);
+void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const double *u,
+                         const double *lambda, const double *params, const snap_stats *stats,
+                         const SampleDerived *sd, const SliceFactor *cache, double *grad_u_hat,
+                         double *grad_params, BwdContrib *contrib, cudaStream_t s);
 void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *params,
                      const SampleDerived *sd, double *u, double *lambda, BlockStat *bst,
                      SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s);
