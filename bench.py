@@ -34,7 +34,8 @@ WORKLOAD = dict(name="burgers_1d", family="B", B=512, nx=128, nt=100, seed=1001)
 H_TOL = 1e-8
 ROTATE = 4
 KERNEL = "k1d_mixed"                                   # dominant kernel of a step
-KERNEL_SOURCE = "paper_2607_00095_b300/csrc/kern_1d_mixed.cu"
+KERNEL_SOURCES = ("paper_2607_00095_b300/csrc/kern_1d_mixed.cu", "paper_2607_00095_b300/csrc/slice_newton.cuh",
+                  "paper_2607_00095_b300/csrc/df64.cuh", "paper_2607_00095_b300/csrc/snap_internal.h")
 
 
 def parse():
@@ -117,15 +118,21 @@ def measured_peaks():
         return {}
 
 
-def kernel_traffic(name, source):
+def sources_digest(sources):
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, src), "rb").read())
+    return h.hexdigest()
+
+
+def kernel_traffic(name, sources):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
     try:
         rec = json.load(open(path))
     except (OSError, ValueError):
         return None
-    h = hashlib.sha256(open(os.path.join(ROOT, source), "rb").read()).hexdigest()
-    if rec.get("source_sha256") != h:
+    if rec.get("source_sha256") != sources_digest(sources):
         return None
     return rec.get("traffic_bytes_per_launch_full_size")
 
@@ -374,7 +381,7 @@ def run_ours(args, rank, world, local):
     launch_bytes = bytes_per_sample * B
     k_avg_ms = k_ms / max(k_n, 1)
     achieved = launch_bytes / (k_avg_ms / 1e3) / 1e9
-    traffic = kernel_traffic(KERNEL, KERNEL_SOURCE)
+    traffic = kernel_traffic(KERNEL, KERNEL_SOURCES)
     fp64 = api.measure_fp64_rate(local)
 
     cpu = None
