@@ -940,3 +940,8 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
   snap_note_launch(launches);
   return cudaGetLastError();
 }
+
+void launch_finalize_stats(int B, int nblk, const BlockStat *bst, double tol_h, snap_stats *stats,
+                           cudaStream_t s) {
+  k_finalize_stats<<<warps_blocks(B), 128, 0, s>>>(B, nblk, bst, nullptr, tol_h, stats);
+}

@@ -244,6 +244,10 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
         free(p);
         return fail(SNAP_ERR_INVALID_ARG, "2-D grid must be square, even, in [4, 1024]");
       }
+      if (!supported_2d(d->nx)) {
+        free(p);
+        return fail(SNAP_ERR_UNSUPPORTED, "2-D grid side must be 4, 8, 16, 32 or 64 in this build");
+      }
       const int N = d->nx;
       p->info.n_vars = 2 * N * N * d->nt;
       p->info.n_rows_nominal = N * N * d->nt + d->nt;
@@ -360,6 +364,7 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
   else
     e = launch_1d_forward(p, B, u_hat, params, u0, u, lambda, stats, adjoint_cache, so, path,
                           workspace, (cudaStream_t)stream);
+  if (e == cudaErrorNotSupported) return fail(SNAP_ERR_UNSUPPORTED, "unsupported request for this family");
   if (e != cudaSuccess) return cuda_fail(e, "snap_project launch");
   return SNAP_OK;
 }

@@ -129,6 +129,9 @@ cudaError_t launch_2d_residual(const snap_problem *p, int B, const double *w,
                                const double *params, double *h, double *h_inf, void *ws,
                                cudaStream_t s);
 size_t ws_bytes_2d(const snap_problem *p, int B);
+bool supported_2d(int N);
+void launch_finalize_stats(int B, int nblk, const BlockStat *bst, double tol_h, snap_stats *stats,
+                           cudaStream_t s);
 size_t cache_bytes_2d(const snap_problem *p, int B);
 
 // Alignment helper for workspace carving.
