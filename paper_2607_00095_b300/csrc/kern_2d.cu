@@ -73,39 +73,62 @@ static void class_eigen(int M, std::vector<double> &Q, std::vector<double> &thet
   if (M % 2 == 0 && M >= 2) set_col(col++, M / 2, false, 1.0 / sqrt((double)M));
 }
 
-cudaError_t setup_2d(snap_problem *p) {
-  const int N = p->desc.nx;
-  const int M = N / 2;
-  std::vector<double> Q, th;
-  class_eigen(M, Q, th);
-  std::vector<float> hQ((size_t)M * M), hinv((size_t)M * M);
-  for (int i = 0; i < M * M; ++i) hQ[i] = (float)Q[i];
-  for (int a = 0; a < M; ++a)
-    for (int b = 0; b < M; ++b) {
-      const double e = th[a] + th[b];
-      hinv[(size_t)a * M + b] = (a == 0 && b == 0) ? 0.0f : (float)(1.0 / e);
-    }
-  const size_t bytes = sizeof(float) * (size_t)M * M * 2;
+// Host copy of the factor, uploaded on create (or on first use when the create call ran
+// without a usable device, e.g. a host-only pattern query).
+struct Host2D {
+  std::vector<float> Qinv;   // [Q | inv], 2 M^2 floats
+};
+
+static cudaError_t upload_2d(snap_problem *p) {
+  Host2D *h = (Host2D *)p->host_const;
+  if (!h) return cudaErrorInvalidValue;
+  const size_t bytes = sizeof(float) * h->Qinv.size();
   void *d = nullptr;
   cudaError_t e = cudaMalloc(&d, bytes);
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpy(d, hQ.data(), sizeof(float) * (size_t)M * M, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy((char *)d + sizeof(float) * (size_t)M * M, hinv.data(),
-                   sizeof(float) * (size_t)M * M, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  e = cudaMemcpy(d, h->Qinv.data(), bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(d);
     return e;
   }
   p->dev_const = d;
   p->dev_const_bytes = bytes;
-  p->n2d_m = M;
   return cudaSuccess;
+}
+
+cudaError_t setup_2d(snap_problem *p) {
+  const int N = p->desc.nx;
+  const int M = N / 2;
+  std::vector<double> Q, th;
+  class_eigen(M, Q, th);
+  Host2D *h = new Host2D;
+  h->Qinv.resize((size_t)2 * M * M);
+  for (int i = 0; i < M * M; ++i) h->Qinv[i] = (float)Q[i];
+  for (int a = 0; a < M; ++a)
+    for (int b = 0; b < M; ++b) {
+      const double e = th[a] + th[b];
+      h->Qinv[(size_t)M * M + (size_t)a * M + b] = (a == 0 && b == 0) ? 0.0f : (float)(1.0 / e);
+    }
+  p->host_const = h;
+  p->n2d_m = M;
+  upload_2d(p);      // a failure here is reported by the first compute call
+  return cudaSuccess;
+}
+
+// Device copy of the factor for a compute call (uploaded now if create could not).
+static cudaError_t ensure_2d(const snap_problem *p) {
+  if (p->dev_const) return cudaSuccess;
+  return upload_2d(const_cast<snap_problem *>(p));
 }
 
 void teardown_2d(snap_problem *p) {
   if (p->dev_const) cudaFree(p->dev_const);
   p->dev_const = nullptr;
+  delete (Host2D *)p->host_const;
+  p->host_const = nullptr;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -759,6 +782,8 @@ cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
   (void)cache;
   (void)path;
   if (w0) return cudaErrorNotSupported;
+  cudaError_t eu = ensure_2d(p);
+  if (eu != cudaSuccess) return eu;
   Ws2D wk = carve_2d(p, B, ws);
   const int N = p->desc.nx;
   cudaError_t e;
@@ -787,6 +812,8 @@ cudaError_t launch_2d_backward(const snap_problem *p, int B, const double *grad_
                                const snap_stats *stats, const void *cache, double *grad_w_hat,
                                double *grad_params, void *ws, cudaStream_t s) {
   (void)cache;
+  cudaError_t eu = ensure_2d(p);
+  if (eu != cudaSuccess) return eu;
   Ws2D wk = carve_2d(p, B, ws);
   const int N = p->desc.nx;
   cudaError_t e;

@@ -85,6 +85,7 @@ struct snap_problem {
   // 2-D: constant Schur factor of the divergence rows (device), see kern_2d.cu
   void *dev_const;
   size_t dev_const_bytes;
+  void *host_const;    // host copy of the 2-D factor (uploaded on create or first use)
   int n2d_band;        // half bandwidth of the class factor
   int n2d_m;           // unknowns of one parity-class system (M*M - 1)
 };
