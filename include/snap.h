@@ -252,6 +252,36 @@ SNAP_API snap_status snap_constraint_residual(snap_problem_t p, int B, const dou
                                      void *workspace, size_t workspace_bytes,
                                      snap_stream_t stream);
 
+/* ---------------- forward projection without any allocation ---------------- */
+
+/* Bytes of the library's static device scratch used by snap_project_noalloc (8 MiB). */
+#define SNAP_NOALLOC_SCRATCH_BYTES 8388608
+
+/* The 1-D forward projection of snap_project (families A and B, start u0 = u_hat, the path of
+ * opt->path or the mixed-pipe path for AUTO/GENERAL), with its scratch memory taken from a
+ * fixed library-owned device array instead of a caller-provided workspace.  The paper has no
+ * counterpart; this entry point exists for callers that cannot allocate device memory where
+ * they project (a host callback or plugin where cudaMalloc is not permitted, or an embedding
+ * with no allocator of its own that cannot size a workspace per batch).  The caller still
+ * passes all inputs and outputs, with the meaning and layout of snap_project; no adjoint cache.
+ *   - It calls no cudaMalloc / cudaFree or any other allocating routine.
+ *   - Limit: snap_workspace_size(p, B) must not exceed SNAP_NOALLOC_SCRATCH_BYTES (about
+ *     80 bytes per time slice plus 64 per sample: e.g. B * nt <= 100,000 slices); larger
+ *     batches are rejected with SNAP_ERR_WORKSPACE and a message.
+ *   - The scratch is one file-scope __device__ array: every GPU that loads the library holds
+ *     it until the process exits.  The first call on a device looks up its device address
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the previous call's contents; nothing in it needs
+ *     to start at zero (every byte a call reads was written earlier in the same call).  Calls
+ *     whose work overlaps on the GPU (other streams, other threads) race on the array: order
+ *     them on one stream or synchronise between them.
+ * Errors: as snap_project, plus UNSUPPORTED for the 2-D family. */
+SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double *u_hat,
+                                          const double *params, double *u, double *lambda,
+                                          snap_stats *stats, const snap_options *opt,
+                                          snap_stream_t stream);
+
 /* ---------------- uneven batches in one persistent launch ---------------- */
 
 /* A batch of n_inst instances; instance i is one sample of problem probs[inst_problem[i]]

@@ -6,6 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsnap.so")
 
 SNAP_OK = 0
+NOALLOC_SCRATCH_BYTES = 8388608
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NO_MEMORY",
                 5: "WORKSPACE", 6: "NOT_READY"}
 FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY = 0, 1, 2, 3
@@ -59,6 +60,7 @@ _PROTOS = {
     "snap_project_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         _vp, C.c_size_t, _vp]),
     "snap_constraint_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "snap_project_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.POINTER(Options), _vp]),
     "snap_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp), C.c_int, _ip, C.POINTER(_vp)]),
     "snap_batch_destroy": (None, [_vp]),
     "snap_batch_bind": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),

@@ -142,6 +142,19 @@ class Problem:
                                  ws.numel(), _stream(stream)))
         return u, lam, st, cb
 
+    def project_noalloc(self, u_hat, params, u, lam, st, opts=None, stream=None):
+        """snap_project_noalloc: the 1-D forward projection into caller-given outputs, with the
+        scratch in the library's static device array (no workspace, nothing allocated by the
+        call).  Calls that overlap on the GPU race on that array."""
+        B = u_hat.shape[0]
+        self._check_dev(u_hat, params, u, lam)
+        if not st.is_cuda or st.dtype != torch.uint8 or st.numel() != 40 * B:
+            raise ValueError("stats must be a CUDA uint8 tensor of 40 bytes per sample")
+        o = opts if opts is not None else options()
+        check(lib().snap_project_noalloc(self._h, B, _ptr(u_hat), _ptr(params), _ptr(u),
+                                         _ptr(lam), _ptr(st), C.byref(o), _stream(stream)))
+        return u, lam, st
+
     def backward(self, grad_u, u, lam, params, stats=None, cache=None, stream=None,
                  with_params=True):
         B = u.shape[0]

@@ -161,6 +161,10 @@ size_t ws_bytes(const snap_problem *p, int B) {
 
 void snap_note_launch(int n) { g_launches += n; }
 
+snap_status snap_fail_msg(snap_status st, const char *msg) { return fail(st, "%s", msg); }
+
+snap_status snap_check_options(const snap_options &o) { return check_opts(o); }
+
 extern "C" {
 
 const char *snap_last_error(void) { return g_err; }

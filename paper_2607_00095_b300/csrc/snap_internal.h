@@ -90,6 +90,10 @@ struct snap_problem {
   int n2d_m;           // unknowns of one parity-class system (M*M - 1)
 };
 
+// Error-message helpers of snap_api.cu for the other entry-point files.
+snap_status snap_fail_msg(snap_status st, const char *msg);
+snap_status snap_check_options(const snap_options &o);
+
 // Kernel-launch bookkeeping (per host thread) and optional event timing (snap_profile.cu).
 void snap_note_launch(int n);
 int snap_prof_begin(cudaStream_t s, const char *name);
