@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the 2-D and uneven-batch measurements reported beside the headline")
+    ap.add_argument("--extra-only", action="store_true",
+                    help="run only the 2-D and uneven-batch measurements (one JSON line)")
     return ap.parse_args()
 
 
@@ -205,6 +209,11 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    if args.extra_only:
+        hbm0 = measured_peaks().get("hbm_gbs") or 6400.0
+        print(json.dumps({"div_2d": measure_div2d(dev, hbm0), "uneven": measure_uneven(dev)}),
+              flush=True)
+        return 0
     w = WORKLOAD
     B, nx, nt = w["B"], w["nx"], w["nt"]
     p = Problem(w["family"], nx, nt)
@@ -384,6 +393,11 @@ def run_ours(args, rank, world, local):
     traffic = kernel_traffic(KERNEL, KERNEL_SOURCES)
     fp64 = api.measure_fp64_rate(local)
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra:
+        extra["div_2d"] = measure_div2d(dev, hbm)
+        extra["uneven"] = measure_uneven(dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import solve
@@ -417,10 +431,149 @@ def run_ours(args, rank, world, local):
             "gpu_launches": launches,
             "clocks": clk,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _event_ms(fn, reps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_div2d(dev, hbm, reps=50):
+    """The 2-D velocity workload: B=64 samples of (u, v) on 64 x 64 x 16 frames (divergence
+    rows + kinetic energy); two rotating sets (2 x 134 MB in + out > L2), CUDA graphs."""
+    import torch
+
+    from paper_2607_00095_b300 import Problem, api, decode_stats, synthetic
+    w = synthetic.WORKLOADS["div_2d"]
+    B, N, nt = w["B"], w["N"], w["nt"]
+    p = Problem("C", N, nt)
+    sets = []
+    for r in range(2):
+        wh, pr = synthetic.gen_2d(w["seed"] + 7919 * r, B, N, nt)
+        d_wh = torch.as_tensor(wh.reshape(B, -1), device=dev)
+        d_pr = torch.as_tensor(pr, device=dev)
+        out = (torch.empty_like(d_wh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        sets.append((d_wh, d_pr, out))
+    ws = p.workspace(B, dev)
+    for d_wh, d_pr, out in sets:
+        p.project(d_wh, d_pr, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    api.profile_reset()
+    api.profile_enable(1)
+    for i in range(10):
+        d_wh, d_pr, out = sets[i % 2]
+        p.project(d_wh, d_pr, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    k_ms, k_n = api.profile_read("k2d_frame")
+    api.profile_enable(0)
+    api.profile_reset()
+    cap = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(cap):
+        for d_wh, d_pr, out in sets:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                p.project(d_wh, d_pr, out=out, workspace=ws, stream=cap)
+            graphs.append(g)
+    for g in graphs:
+        g.replay()
+    it = [0]
+
+    def step():
+        graphs[it[0] % 2].replay()
+        it[0] += 1
+    ms = _event_ms(step, reps)
+    conv = 0
+    for d_wh, d_pr, out in sets:
+        _, hinf = p.residual(out[0], d_pr, want_rows=False)
+        st = decode_stats(out[2])
+        conv += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+    conv /= 2
+    bytes_per_call = (8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40) * B
+    kavg = k_ms / max(k_n, 1)
+    return {"workload": "div_2d", "B": B, "N": N, "nt": nt, "ms_per_call": ms,
+            "converged_per_call": conv, "projections_per_s": conv / (ms / 1e3),
+            "kernel": "k2d_frame", "kernel_ms": kavg,
+            "hbm_frac_of_measured": bytes_per_call / (kavg / 1e3) / 1e9 / hbm,
+            "algorithmic_bytes_per_call": bytes_per_call,
+            "note": "FP32-pipe bound (four M x M products per class per refinement round)"}
+
+
+def measure_uneven(dev, reps=30):
+    """The uneven mix: 1024 instances (seed 1004), 75 % family B with nx in {64, 96, 128, 192,
+    256} and nt in {50, 100, 200}, the rest 2-D at 32 x 32 x 8; inputs 140 MB (> L2).  One
+    persistent launch (autotuned schedule, library-owned CUDA graph) against one plain launch
+    per (family, size) group (the same calls captured in a CUDA graph)."""
+    import numpy as np
+    import torch
+
+    from paper_2607_00095_b300 import Batch, Problem, decode_stats, synthetic
+    mix = synthetic.gen_uneven(**synthetic.WORKLOADS["uneven"])
+    keys = sorted({(m["family"], m["nx"], m["nt"]) for m in mix})
+    probs = [Problem(f, nx, nt) for f, nx, nt in keys]
+    inst = np.array([keys.index((m["family"], m["nx"], m["nt"])) for m in mix], np.int32)
+    b = Batch(probs, inst)
+    bufs = b.alloc(dev)
+    in_bytes = 0
+    for pi, g in bufs.items():
+        g["uh"].copy_(torch.as_tensor(np.stack([mix[i]["u_hat"].reshape(-1) for i in g["ids"]])))
+        g["pr"].copy_(torch.as_tensor(np.stack([mix[i]["params"] for i in g["ids"]])))
+        in_bytes += g["uh"].numel() * 8
+    sched, tune_ms = b.autotune(reps=5)
+    n = len(mix)
+    t_ns = torch.zeros(n, 2, dtype=torch.int64, device=dev)
+    b.capture_graph(t_ns=t_ns)
+    for _ in range(3):
+        b.launch_graph()
+    ms_p = _event_ms(b.launch_graph, reps)
+    tt = t_ns.cpu().numpy().astype(np.float64)
+    lat_us = (tt[:, 1] - tt[:, 0]) / 1e3
+    makespan_us = (tt[:, 1].max() - tt[:, 0].min()) / 1e3
+
+    def converged():
+        c = 0
+        for pi, g in bufs.items():
+            _, hinf = probs[pi].residual(g["u"], g["pr"], want_rows=False)
+            st = decode_stats(g["st"])
+            c += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+        return c
+    conv_p = converged()
+    cap = torch.cuda.Stream()
+    b.project_grouped()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cap):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=cap):
+            b.project_grouped(stream=cap)
+    g.replay()
+    ms_g = _event_ms(g.replay, reps)
+    conv_g = converged()
+    return {"workload": "uneven", "instances": n, "groups": len(keys),
+            "schedule": sched, "autotune_best_ms": tune_ms,
+            "persistent_ms_per_call": ms_p, "grouped_ms_per_call": ms_g,
+            "speedup_vs_grouped": ms_g / ms_p,
+            "converged_persistent": conv_p, "converged_grouped": conv_g,
+            "projections_per_s": conv_p / (ms_p / 1e3),
+            "grouped_projections_per_s": conv_g / (ms_g / 1e3),
+            "latency_us_p50": float(np.percentile(lat_us, 50)),
+            "latency_us_p99": float(np.percentile(lat_us, 99)),
+            "makespan_us": makespan_us, "input_bytes": in_bytes,
+            "persistent_launches_per_call": 1,
+            "grouped_launches_per_call": sum(2 if f == "C" else 3 for f, _, _ in keys)}
 
 
 def lib_project_cache(p, d_uh, d_pr, opts, out, cache, ws):

@@ -284,31 +284,88 @@ SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double 
 
 /* ---------------- uneven batches in one persistent launch ---------------- */
 
-/* A batch of n_inst instances; instance i is one sample of problem probs[inst_problem[i]]
- * (host arrays).  The problems must outlive the batch.  All instance sizes may differ. */
+/* A batch of instances of differing grid sizes and constraint families, projected together
+ * (the block-diagonal batch of independent samples of Section 3, "Jacobian Structure",
+ * extended to samples of different shapes and families): instance
+ * i is one sample of problem probs[inst_problem[i]].  Supported families: A and B (1-D, the
+ * mixed-pipe moment path, start u0 = u_hat) and C (2-D).  Instances of one problem form a
+ * group; groups differ in shape.  snap_batch_project runs every instance in ONE persistent
+ * kernel launch (after one memset of the workspace header): 2-D frames are taken from a work
+ * queue by whole blocks, 1-D tiles of 32 time slices by single warps, and the last unit of an
+ * instance to finish reduces that instance's statistics.  No allocation, no synchronisation:
+ * capturable in a CUDA graph (see snap_batch_capture_graph).  Results are those of
+ * snap_project on each instance (the same device code runs per slice / frame). */
+
+/* How the persistent launch orders and shapes its work (the autotuner's search space). */
+typedef struct {
+  int ctas_per_sm;   /* resident blocks of 256 threads per SM (1 or 2; clamped to occupancy) */
+  int order;         /* 0: 2-D frames first, then 1-D tiles;  1: 1-D tiles first */
+  int pack_1d;       /* 1: a 1-D tile's 32 slices may span consecutive instances of a group;
+                        0: tiles end at instance boundaries */
+  int sort_1d;       /* 1-D groups in the queue: 0 creation order, 1 widest grid (nx) first */
+} snap_batch_schedule;
+
+/* Host arrays probs[n_problems], inst_problem[n_inst]; the problems must outlive the batch.
+ * Allocates the batch's device tables on the current device (bind and project use it).
+ * Errors: INVALID_ARG (null arrays, index out of range, n_inst < 0), UNSUPPORTED (a family
+ * other than A, B, C), NO_MEMORY / CUDA (device allocation). */
 SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *probs, int n_inst,
-                              const int *inst_problem, snap_batch_t *out);
+                                       const int *inst_problem, snap_batch_t *out);
 SNAP_API void snap_batch_destroy(snap_batch_t b);
 
-/* Bind the device buffers of every instance (host arrays of device pointers, length
- * n_inst).  Copies the pointer table to the device synchronously; call again to rebind.
- * lambda and stats rows are per instance. */
+/* Bind the device buffers of every instance (host arrays of device pointers, length n_inst):
+ * u_hat[i] / u[i] [n_vars], params[i] [n_params], lambda[i] [n_rows_nominal], stats[i] one
+ * snap_stats (layouts as in snap_project for one sample).  1-D u_hat / u must be 16-byte
+ * aligned, everything else 8-byte aligned.  Copies the pointer table to the device
+ * synchronously; call again to rebind (a captured graph then uses the new pointers).
+ * Errors: INVALID_ARG (null or misaligned pointer; the message names the instance). */
 SNAP_API snap_status snap_batch_bind(snap_batch_t b, const double *const *u_hat,
-                            const double *const *params, double *const *u,
-                            double *const *lambda, snap_stats *stats);
+                                     const double *const *params, double *const *u,
+                                     double *const *lambda, snap_stats *const *stats);
 
-/* Workspace for snap_batch_project. */
+/* Workspace of snap_batch_project and snap_batch_project_grouped (device, 256-byte aligned). */
 SNAP_API snap_status snap_batch_workspace_size(snap_batch_t b, size_t *bytes);
 
-/* Project every bound instance in ONE persistent kernel launch: blocks pull work items
- * (instance, block range) from a queue in the workspace.  t_ns (device, [n_inst][2]) or
- * NULL receives each instance's first-start and last-end %globaltimer stamps. */
-SNAP_API snap_status snap_batch_project(snap_batch_t b, const snap_options *opt, unsigned long long *t_ns,
-                               void *workspace, size_t workspace_bytes, snap_stream_t stream);
+/* Project every bound instance in one persistent launch on stream.  t_ns (device,
+ * [n_inst][2]) or NULL receives each instance's first-start and finish %globaltimer stamps
+ * (ns).  opt: as snap_project (the path field is ignored).  Errors: NOT_READY (unbound),
+ * WORKSPACE, INVALID_ARG (options), CUDA. */
+SNAP_API snap_status snap_batch_project(snap_batch_t b, const snap_options *opt,
+                                        unsigned long long *t_ns, void *workspace,
+                                        size_t workspace_bytes, snap_stream_t stream);
 
-/* Same work as snap_batch_project but one plain launch per (family, size) group. */
-SNAP_API snap_status snap_batch_project_grouped(snap_batch_t b, const snap_options *opt, void *workspace,
-                                       size_t workspace_bytes, snap_stream_t stream);
+/* The same work as snap_batch_project as plain snap_project launches, one per group (the
+ * comparison baseline).  Needs each group's bound buffers to be contiguous and in instance
+ * order (instance j+1 of a group directly after instance j, in every array); else
+ * UNSUPPORTED. */
+SNAP_API snap_status snap_batch_project_grouped(snap_batch_t b, const snap_options *opt,
+                                                void *workspace, size_t workspace_bytes,
+                                                snap_stream_t stream);
+
+/* Current schedule / set one (host only: rebuilds and uploads the work lists, synchronous). */
+SNAP_API snap_status snap_batch_get_schedule(snap_batch_t b, snap_batch_schedule *s);
+SNAP_API snap_status snap_batch_set_schedule(snap_batch_t b, const snap_batch_schedule *s);
+
+/* Autotuner: times snap_batch_project (CUDA events on stream, `reps` launches after one
+ * warm-up, best of them) for every schedule of the search space, keeps the fastest on the
+ * batch and returns it in *best (and its time in *best_ms, either may be NULL).  Runs the
+ * projection on the bound buffers (outputs are overwritten with the same results);
+ * synchronous.  Errors: as snap_batch_project. */
+SNAP_API snap_status snap_batch_autotune(snap_batch_t b, const snap_options *opt, void *workspace,
+                                         size_t workspace_bytes, snap_stream_t stream, int reps,
+                                         snap_batch_schedule *best, double *best_ms);
+
+/* Capture snap_batch_project(b, opt, t_ns, workspace) into a CUDA graph owned by the batch
+ * (replacing an earlier one) / launch that graph on stream.  The graph reads the bound
+ * pointer table when it runs, so rebinding needs no new capture; a new schedule does. */
+SNAP_API snap_status snap_batch_capture_graph(snap_batch_t b, const snap_options *opt,
+                                              unsigned long long *t_ns, void *workspace,
+                                              size_t workspace_bytes);
+SNAP_API snap_status snap_batch_launch_graph(snap_batch_t b, snap_stream_t stream);
+
+/* Shape of the batch: groups, 1-D tiles and 2-D frames in the current schedule's queues. */
+SNAP_API snap_status snap_batch_info(snap_batch_t b, int *n_groups, int *n_tiles_1d,
+                                     int *n_frames_2d);
 
 /* ---------------- measurement helpers ---------------- */
 

@@ -38,6 +38,11 @@ class Options(C.Structure):
                 ("max_corrections", C.c_int), ("path", C.c_int), ("w_keep", C.c_double)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int), ("order", C.c_int), ("pack_1d", C.c_int),
+                ("sort_1d", C.c_int)]
+
+
 assert C.sizeof(Stats) == 40
 
 _lib = None
@@ -64,10 +69,17 @@ _PROTOS = {
     "snap_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp), C.c_int, _ip, C.POINTER(_vp)]),
     "snap_batch_destroy": (None, [_vp]),
     "snap_batch_bind": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
-                                  C.POINTER(_vp), _vp]),
+                                  C.POINTER(_vp), C.POINTER(_vp)]),
     "snap_batch_workspace_size": (C.c_int, [_vp, C.POINTER(C.c_size_t)]),
     "snap_batch_project": (C.c_int, [_vp, C.POINTER(Options), _vp, _vp, C.c_size_t, _vp]),
     "snap_batch_project_grouped": (C.c_int, [_vp, C.POINTER(Options), _vp, C.c_size_t, _vp]),
+    "snap_batch_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "snap_batch_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "snap_batch_autotune": (C.c_int, [_vp, C.POINTER(Options), _vp, C.c_size_t, _vp, C.c_int,
+                                      C.POINTER(Schedule), _dp]),
+    "snap_batch_capture_graph": (C.c_int, [_vp, C.POINTER(Options), _vp, _vp, C.c_size_t]),
+    "snap_batch_launch_graph": (C.c_int, [_vp, _vp]),
+    "snap_batch_info": (C.c_int, [_vp, _ip, _ip, _ip]),
     "snap_measure_fp64_rate": (C.c_int, [C.c_int, _dp]),
     "snap_last_launch_count": (C.c_int, []),
     "snap_profile_enable": (C.c_int, [C.c_int]),

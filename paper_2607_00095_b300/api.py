@@ -211,6 +211,133 @@ class SnapProject(torch.autograd.Function):
         return gh.reshape(ctx.shape), gp, None, None, None
 
 
+def _schedule_dict(s):
+    return dict(ctas_per_sm=s.ctas_per_sm, order=s.order, pack_1d=s.pack_1d, sort_1d=s.sort_1d)
+
+
+class Batch:
+    """Uneven batch (snap_batch_*): instances of several problems (1-D families A/B, 2-D
+    family C) projected in one persistent kernel launch.  Instance i is one sample of
+    problems[inst_problem[i]]."""
+
+    def __init__(self, problems, inst_problem):
+        self.problems = list(problems)
+        self.inst_problem = np.ascontiguousarray(inst_problem, dtype=np.int32)
+        n = int(self.inst_problem.size)
+        arr = (C.c_void_p * len(self.problems))(*[p._h.value for p in self.problems])
+        h = C.c_void_p()
+        check(lib().snap_batch_create(len(self.problems), arr, n,
+                                      self.inst_problem.ctypes.data_as(C.POINTER(C.c_int)),
+                                      C.byref(h)))
+        self._h = h
+        self.n_inst = n
+        self._keep = None
+        self._ws = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _abi._lib is not None:
+            _abi._lib.snap_batch_destroy(h)
+            self._h = None
+
+    def groups(self):
+        """{problem index: instance ids of that problem, in instance order}."""
+        return {int(pi): np.nonzero(self.inst_problem == pi)[0]
+                for pi in np.unique(self.inst_problem)}
+
+    def alloc(self, device):
+        """Allocate contiguous per-group buffers (u_hat, params, u, lambda, stats), bind them and
+        return {problem index: dict(ids, uh, pr, u, lam, st)} (row j = instance ids[j])."""
+        out = {}
+        per = [None] * self.n_inst
+        for pi, ids in self.groups().items():
+            p = self.problems[pi]
+            n = len(ids)
+            g = dict(ids=ids,
+                     uh=torch.zeros(n, p.n_vars, dtype=torch.float64, device=device),
+                     pr=torch.zeros(n, p.n_params, dtype=torch.float64, device=device),
+                     u=torch.empty(n, p.n_vars, dtype=torch.float64, device=device),
+                     lam=torch.empty(n, p.n_rows, dtype=torch.float64, device=device),
+                     st=torch.empty(n, 40, dtype=torch.uint8, device=device))
+            out[pi] = g
+            for j, i in enumerate(ids):
+                per[i] = (g["uh"][j], g["pr"][j], g["u"][j], g["lam"][j], g["st"][j])
+        self.bind(*[[x[k] for x in per] for k in range(5)])
+        return out
+
+    def bind(self, u_hat, params, u, lam, stats):
+        """Bind per-instance device tensors (lists of length n_inst)."""
+        n = self.n_inst
+
+        def tab(ts):
+            return (C.c_void_p * max(n, 1))(*[t.data_ptr() for t in ts])
+
+        tabs = [tab(t) for t in (u_hat, params, u, lam, stats)]
+        check(lib().snap_batch_bind(self._h, *tabs))
+        self._keep = (u_hat, params, u, lam, stats)
+
+    def workspace_bytes(self):
+        n = C.c_size_t()
+        check(lib().snap_batch_workspace_size(self._h, C.byref(n)))
+        return n.value
+
+    def workspace(self, device):
+        need = max(self.workspace_bytes(), 8)
+        if self._ws is None or self._ws.numel() < need or self._ws.device != torch.device(device):
+            self._ws = torch.empty(need, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def _dev(self):
+        return self._keep[0][0].device if self._keep and self.n_inst else torch.device("cuda:0")
+
+    def project(self, opts=None, t_ns=None, stream=None):
+        ws = self.workspace(self._dev())
+        o = opts if opts is not None else options()
+        check(lib().snap_batch_project(self._h, C.byref(o), _ptr(t_ns), _ptr(ws), ws.numel(),
+                                       _stream(stream)))
+
+    def project_grouped(self, opts=None, stream=None):
+        ws = self.workspace(self._dev())
+        o = opts if opts is not None else options()
+        check(lib().snap_batch_project_grouped(self._h, C.byref(o), _ptr(ws), ws.numel(),
+                                               _stream(stream)))
+
+    def schedule(self):
+        s = _abi.Schedule()
+        check(lib().snap_batch_get_schedule(self._h, C.byref(s)))
+        return _schedule_dict(s)
+
+    def set_schedule(self, **kw):
+        d = self.schedule()
+        d.update(kw)
+        s = _abi.Schedule(d["ctas_per_sm"], d["order"], d["pack_1d"], d["sort_1d"])
+        check(lib().snap_batch_set_schedule(self._h, C.byref(s)))
+
+    def autotune(self, opts=None, reps=3, stream=None):
+        """Time every schedule, keep the fastest; returns (schedule dict, ms)."""
+        ws = self.workspace(self._dev())
+        o = opts if opts is not None else options()
+        s = _abi.Schedule()
+        ms = C.c_double()
+        check(lib().snap_batch_autotune(self._h, C.byref(o), _ptr(ws), ws.numel(),
+                                        _stream(stream), reps, C.byref(s), C.byref(ms)))
+        return _schedule_dict(s), ms.value
+
+    def capture_graph(self, opts=None, t_ns=None):
+        ws = self.workspace(self._dev())
+        o = opts if opts is not None else options()
+        check(lib().snap_batch_capture_graph(self._h, C.byref(o), _ptr(t_ns), _ptr(ws),
+                                             ws.numel()))
+
+    def launch_graph(self, stream=None):
+        check(lib().snap_batch_launch_graph(self._h, _stream(stream)))
+
+    def info(self):
+        g, t, f = C.c_int(), C.c_int(), C.c_int()
+        check(lib().snap_batch_info(self._h, C.byref(g), C.byref(t), C.byref(f)))
+        return dict(groups=g.value, tiles_1d=t.value, frames_2d=f.value)
+
+
 def project(problem, u_hat, params, **kw):
     """Forward projection; returns (u, lambda, stats as numpy structured array)."""
     u, lam, st, _ = problem.project(u_hat, params, **kw)

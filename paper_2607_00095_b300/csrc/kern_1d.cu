@@ -20,6 +20,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "sample_1d.cuh"
 #include "slice_newton.cuh"
 #include "snap_internal.h"
 
@@ -66,74 +67,12 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= B) return;
   const double *pg = params + (size_t)warp * g.n_params;
-  double s1 = 0.0, s2 = 0.0;
-  for (int i = lane; i < g.nx; i += 32) {
-    const double v = pg[i];
-    s1 += v;
-    s2 = fma(v, v, s2);
-  }
-  s1 = warp_sum(s1);
-  s2 = warp_sum(s2);
-  if (lane == 0) {
-    SampleDerived d;
-    d.M = g.dx * s1;
-    d.E0 = g.dx * s2;
-    d.q = exp(-pg[g.p_rate] / (double)(g.nt - 1));
-    const double fl = d.M * d.M + g.energy_floor;
-    d.Mh = __double2float_rn(d.M);   d.Ml = __double2float_rn(d.M - (double)d.Mh);
-    d.E0h = __double2float_rn(d.E0); d.E0l = __double2float_rn(d.E0 - (double)d.E0h);
-    d.qh = __double2float_rn(d.q);   d.ql = __double2float_rn(d.q - (double)d.qh);
-    d.fh = __double2float_rn(fl);    d.fl = __double2float_rn(fl - (double)d.fh);
-    // rows at t = 0 evaluated at u_0 = g
-    double hinf = 0.0;
-    if (g.rows & SL_MASS) hinf = nan_max(hinf, fabs(g.dx * s1 - d.M));
-    if (g.rows & SL_ENERGY) {
-      const double e0 = d.E0 >= d.M * d.M + g.energy_floor ? d.E0 : d.M * d.M + g.energy_floor;
-      hinf = nan_max(hinf, fabs(g.dx * s2 - e0));
-    }
-    if (g.rows & SL_BOUND) {
-      const double g0 = pg[0], gh = pg[g.ih];
-      hinf = nan_max(hinf, fabs(g0 * g0 + gh * gh - pg[g.p_c]));
-    }
-    d.h0_inf = hinf;
-    sd[warp] = d;
-  }
-  if (ic_u) {
-    // IC block of this sample (slice k = 0, u0 = u_hat): the rows u_i - g_i are linear and
-    // independent per variable, so one Newton step from (u_hat, 0) lands on u = g,
-    // lambda = u_hat - g (no step when u_hat already satisfies them to tol_kkt)
-    const double *row = ic_uh + (size_t)warp * g.n_vars;
-    double mx = 0.0, sq = 0.0;
-    for (int i = lane; i < g.nx; i += 32) {
-      const double dv = row[i] - pg[i];
-      sq = fma(dv, dv, sq);
-      mx = nan_max(mx, fabs(dv));
-    }
-    mx = warp_max(mx);
-    sq = warp_sum(sq);
-    const bool take = !(mx <= tol_kkt);
-    double *out = ic_u + (size_t)warp * g.n_vars;
-    double *lb = ic_lam + (size_t)warp * g.n_rows;
-    for (int i = lane; i < g.nx; i += 32) {
-      out[i] = take ? pg[i] : row[i];
-      lb[i] = take ? row[i] - pg[i] : 0.0;
-    }
-    if (lane == 0) {
-      if (g.off_mass >= 0) lb[g.off_mass] = 0.0;
-      if (g.off_energy >= 0) lb[g.off_energy] = 0.0;
-      if (g.off_bound >= 0) lb[g.off_bound] = 0.0;
-      BlockStat st;
-      st.iters = take ? 1 : 0;
-      st.backtracks = 0;
-      st.corrections = 0;
-      st.status = (mx == mx && !isinf(mx)) ? SNAP_SAMPLE_OK : SNAP_SAMPLE_NONFINITE;
-      st.kkt_inf = take ? 0.0 : mx;
-      // rows at t = 0 implied by the IC rows, evaluated at u_0 = g (computed above)
-      st.h_inf = nan_max(take ? 0.0 : mx, sd[warp].h0_inf);
-      st.obj = take ? 0.5 * sq : 0.0;
-      ic_bst[(size_t)warp * g.nt] = st;
-    }
-  }
+  const SampleDerived d = s1_derive(g, pg, lane);
+  if (lane == 0) sd[warp] = d;
+  if (ic_u)
+    s1_ic_forward(g, pg, ic_uh + (size_t)warp * g.n_vars, ic_u + (size_t)warp * g.n_vars,
+                  ic_lam + (size_t)warp * g.n_rows, ic_bst + (size_t)warp * g.nt, d.h0_inf,
+                  tol_kkt, lane);
   if (bwd_gh) {
     // adjoint on the IC block: K = [I I; I 0] -> a = 0 (b_IC = gbar enters dL/dg later)
     const bool bad = bwd_st && bwd_st[warp].status != SNAP_SAMPLE_OK;
@@ -156,43 +95,7 @@ __global__ void k_finalize_stats(int B, int nblk, const BlockStat *__restrict__ 
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= B) return;
   (void)tol_h_ptr;
-  int iters = 0, bt = 0, corr = 0, rank = 0, status = SNAP_SAMPLE_OK;
-  double hinf = 0.0, kinf = 0.0, obj = 0.0;
-  for (int k = lane; k < nblk; k += 32) {
-    const BlockStat q = bs[(size_t)warp * nblk + k];
-    iters = max(iters, q.iters);
-    bt += q.backtracks;
-    corr += q.corrections;
-    const int rk = snap_status_rank(q.status);
-    if (rk > rank) { rank = rk; status = q.status; }
-    hinf = nan_max(hinf, q.h_inf);
-    kinf = nan_max(kinf, q.kkt_inf);
-    obj += q.obj;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    iters = max(iters, __shfl_xor_sync(FULL, iters, o));
-    bt += __shfl_xor_sync(FULL, bt, o);
-    corr += __shfl_xor_sync(FULL, corr, o);
-    const int r2 = __shfl_xor_sync(FULL, rank, o);
-    const int s2 = __shfl_xor_sync(FULL, status, o);
-    if (r2 > rank || (r2 == rank && s2 < status)) { rank = r2; status = s2; }
-  }
-  hinf = warp_max(hinf);
-  kinf = warp_max(kinf);
-  obj = warp_sum(obj);
-  if (lane == 0) {
-    snap_stats st;
-    st.iters = iters;
-    st.backtracks = bt;
-    st.corrections = corr;
-    st.status = status;
-    if (status == SNAP_SAMPLE_OK && !(hinf <= tol_h)) st.status = SNAP_SAMPLE_RESIDUAL;
-    st.h_inf = hinf;
-    st.kkt_inf = kinf;
-    st.obj = obj;
-    out[warp] = st;
-  }
+  s1_finalize<false>(bs + (size_t)warp * nblk, nblk, tol_h, out + warp, lane);
 }
 
 }  // namespace

@@ -121,6 +121,7 @@ void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *
                      SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s);
 
 cudaError_t setup_2d(snap_problem *p);
+cudaError_t ensure_2d_factor(const snap_problem *p);
 void teardown_2d(snap_problem *p);
 cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
                               const double *params, const double *w0, double *w, double *lambda,
