@@ -65,6 +65,9 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
                            double *__restrict__ bwd_gp, const snap_stats *__restrict__ bwd_st) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // a kernel launched as this one's programmatic dependent may start now (it waits for this
+  // kernel's completion before it reads anything written here)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (warp >= B) return;
   const double *pg = params + (size_t)warp * g.n_params;
   const SampleDerived d = s1_derive(g, pg, lane);
@@ -93,6 +96,8 @@ __global__ void k_finalize_stats(int B, int nblk, const BlockStat *__restrict__ 
                                  snap_stats *__restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // launched as a programmatic dependent of the tile kernel: wait for its statistics
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (warp >= B) return;
   (void)tol_h_ptr;
   s1_finalize<false>(bs + (size_t)warp * nblk, nblk, tol_h, out + warp, lane);
@@ -682,6 +687,8 @@ __global__ void k1d_backward_params(Geom1D g, int B, const double *__restrict__ 
                                     double *__restrict__ gp) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  // launched as a programmatic dependent of the adjoint tile kernel: wait for its output
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   if (warp >= B) return;
   double sm = 0.0, sex = 0.0, sfl = 0.0, sr = 0.0;
   for (int k = 1 + lane; k < g.nt; k += 32) {
@@ -797,7 +804,7 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   }
   launches++;
   if (stats) {
-    k_finalize_stats<<<warps_blocks(B), 128, 0, s>>>(B, g.nt, w.bst, nullptr, o.tol_h, stats);
+    launch_finalize_stats(B, g.nt, w.bst, o.tol_h, stats, s);
     launches++;
   }
   snap_note_launch(launches);
@@ -836,8 +843,18 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
   snap_prof_end(s, pid);
   int launches = 2;
   if (grad_params) {
-    k1d_backward_params<<<warps_blocks(B), 128, 0, s>>>(g, B, grad_u, params, stats, w.sd,
-                                                        w.contrib, grad_params);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)warps_blocks(B));
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k1d_backward_params, g, B, grad_u, params, stats,
+                       (const SampleDerived *)w.sd, (const BwdContrib *)w.contrib, grad_params);
     launches++;
   }
   snap_note_launch(launches);
@@ -846,5 +863,16 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
 
 void launch_finalize_stats(int B, int nblk, const BlockStat *bst, double tol_h, snap_stats *stats,
                            cudaStream_t s) {
-  k_finalize_stats<<<warps_blocks(B), 128, 0, s>>>(B, nblk, bst, nullptr, tol_h, stats);
+  // programmatic dependent of the kernel before it (k_finalize_stats waits for its completion)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)warps_blocks(B));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k_finalize_stats, B, nblk, bst, (const double *)nullptr, tol_h, stats);
 }

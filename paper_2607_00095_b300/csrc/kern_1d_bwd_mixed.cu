@@ -76,6 +76,7 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
   const int nx = g.nx, ih = g.ih;
   const bool need_s = cache == nullptr;
   const df64 dxd(g.dx);
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb) {
     const long long sbase = tile << 5;
@@ -138,6 +139,9 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
       if (r == rho) { mg = a_g; mug = a_ug; mu = a_u; muu = a_uu; mok = ok; }
     }
     // ---------------- phase 2: one slice per lane ----------------
+    // launched as a programmatic dependent of k1d_params: phase 1 above overlaps it, the
+    // per-sample values and everything written below wait for its completion
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long s = sbase + 8 * r + q;
     int live = 0;
     double ciw = 0.0, ciwb = 0.0, ckx = 0.0, ck0 = 0.0, ckxb = 0.0, ck0b = 0.0;
@@ -313,6 +317,16 @@ void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const dou
   const long long ntiles = ((long long)B * g.nt + 31) / 32;
   long long blocks = (ntiles + 3) / 4;
   if (blocks > 148LL * 64) blocks = 148LL * 64;
-  k1d_bwd_mixed<<<(int)blocks, 128, 0, s>>>(g, B, grad_u, u, lambda, params, stats, sd, cache,
-                                            grad_u_hat, grad_params, contrib);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, params, stats, sd, cache,
+                     grad_u_hat, grad_params, contrib);
 }

@@ -20,6 +20,11 @@
 // The IC slices (k = 0) are solved by the per-sample prepare kernel (k1d_params), a full
 // warp per slice, and skipped here.
 //
+// Launch overlap: the kernel is launched as a programmatic dependent of k1d_params.  Phase 1
+// reads only u_hat, so it runs while k1d_params is still working; the first read of the
+// per-sample values (phase 2) waits for k1d_params to complete (griddepcontrol.wait).  The
+// kernel in turn lets the statistics kernel launch early (it waits the same way).
+//
 // A slice whose values leave the range of the float-pair representation (|u_hat| outside
 // [2^-74, 2^57], or non-finite) falls back to FP64 moments and the FP64 iteration.
 //
@@ -72,6 +77,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
   const SliceOptsT<float> so_f = slice_opts<float>(o, o.tol_kkt);
   const SliceOptsT<df64> so_d = slice_opts<df64>(o, o.tol_kkt);
   const df64 dxd(g.dx);
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb) {
     const long long sbase = tile << 5;
@@ -162,6 +168,8 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
       }
     }
     // ---------------- phase 2: one slice per lane ----------------
+    // the per-sample values come from k1d_params (programmatic dependency)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const long long s = sbase + 8 * r + q;
     int kind = KIND_NONE;
     double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
@@ -365,5 +373,15 @@ void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *
   long long blocks = (ntiles + 3) / 4;
   if (blocks_per_sm > 0 && blocks > 148LL * blocks_per_sm) blocks = 148LL * blocks_per_sm;
   if (blocks > 148LL * 64) blocks = 148LL * 64;
-  k1d_mixed<<<(int)blocks, 128, 0, s>>>(g, B, u_hat, params, sd, u, lambda, bst, cache, o);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k1d_mixed, g, B, u_hat, params, sd, u, lambda, bst, cache, o);
 }
