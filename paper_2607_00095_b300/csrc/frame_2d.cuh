@@ -116,6 +116,87 @@ __device__ void fd_solve(float *rf, float *tf, const float *Q, const float *inv)
   __syncthreads();
 }
 
+// Register-tiled form of fd_solve for M >= 8 (the same four products, the same order of
+// every dot product, so the same bits): thread t of the block owns one BL x BL block of the
+// output of its class (BL = M / 8; 4 classes x 8 x 8 blocks = 256 threads) and reads each
+// operand row once per k as a short vector instead of twice per multiply-add.  Intermediate
+// products are kept transposed so that both operands of every product are row slices;
+// Qt = Q^T.
+template <int BL>
+__device__ __forceinline__ void fd_row(const float *p, float (&x)[BL]) {
+  if constexpr (BL == 4) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+  } else if constexpr (BL == 2) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    x[0] = v.x; x[1] = v.y;
+  } else {
+#pragma unroll
+    for (int i = 0; i < BL; ++i) x[i] = p[i];
+  }
+}
+
+// acc[i][j] = sum_k A[k][ia + i] B[k][jb + j] over k = 0 .. M-1 (rows of length M), in k order
+template <int M, int BL>
+__device__ __forceinline__ void fd_block(const float *A, const float *Bm, int ia, int jb,
+                                         float (&acc)[BL][BL]) {
+#pragma unroll
+  for (int i = 0; i < BL; ++i)
+#pragma unroll
+    for (int j = 0; j < BL; ++j) acc[i][j] = 0.0f;
+#pragma unroll 4
+  for (int k = 0; k < M; ++k) {
+    float a[BL], b[BL];
+    fd_row<BL>(A + k * M + ia, a);
+    fd_row<BL>(Bm + k * M + jb, b);
+#pragma unroll
+    for (int i = 0; i < BL; ++i)
+#pragma unroll
+      for (int j = 0; j < BL; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+  }
+}
+
+template <int M>
+__device__ void fd_solve_tiled(float *rf, float *tf, const float *Q, const float *Qt,
+                               const float *inv) {
+  constexpr int MM = M * M, BL = M / 8;
+  static_assert(M >= 8 && M % 8 == 0, "tiled class solve needs M = 8 k");
+  const int c = threadIdx.x >> 6, bi = threadIdx.x & 63;
+  const int i0 = (bi >> 3) * BL, j0 = (bi & 7) * BL;
+  float acc[BL][BL];
+  // T = Q^T R, kept as Tt = T^T:  Tt[j][i] = sum_k Q[k][i] R[k][j]
+  fd_block<M, BL>(Q, rf + c * MM, i0, j0, acc);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < BL; ++i)
+#pragma unroll
+    for (int j = 0; j < BL; ++j) tf[c * MM + (j0 + j) * M + i0 + i] = acc[i][j];
+  __syncthreads();
+  // R = (T Q) .* inv:  R[i][n] = sum_p Tt[p][i] Q[p][n]
+  fd_block<M, BL>(tf + c * MM, Q, i0, j0, acc);
+#pragma unroll
+  for (int i = 0; i < BL; ++i)
+#pragma unroll
+    for (int j = 0; j < BL; ++j)
+      rf[c * MM + (i0 + i) * M + j0 + j] = acc[i][j] * inv[(i0 + i) * M + j0 + j];
+  __syncthreads();
+  // T = Q R, kept as T3t = T^T:  T3t[n][k] = sum_m Qt[m][k] R[m][n]
+  fd_block<M, BL>(Qt, rf + c * MM, i0, j0, acc);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < BL; ++i)
+#pragma unroll
+    for (int j = 0; j < BL; ++j) tf[c * MM + (j0 + j) * M + i0 + i] = acc[i][j];
+  __syncthreads();
+  // R = T Q^T:  R[k][j] = sum_n T3t[n][k] Qt[n][j]
+  fd_block<M, BL>(tf + c * MM, Qt, i0, j0, acc);
+#pragma unroll
+  for (int i = 0; i < BL; ++i)
+#pragma unroll
+    for (int j = 0; j < BL; ++j) rf[c * MM + (i0 + i) * M + j0 + j] = acc[i][j];
+  __syncthreads();
+}
+
 // class / class-local coordinates of cell (i, j) of an N = 2M grid
 template <int M>
 __device__ __forceinline__ int cell_slot(int i, int j) {
@@ -214,23 +295,23 @@ __device__ SliceResult newton2d(const Frame2D &F, Z2D &z, E2D &e, const SolverOp
 }
 
 // Dynamic shared memory of one frame (N = 2M): w [2 N^2] double, then float arrays
-// b (hi, lo), z (hi, lo), r, t [4 M^2 = N^2 each], Q, inv [M^2 each], reduction scratch.
+// b (hi, lo), z (hi, lo), r, t [4 M^2 = N^2 each], Q, inv, Q^T [M^2 each], reduction scratch.
 template <int M>
 struct Smem2D {
   static constexpr int N = 2 * M, NN = N * N, MM = M * M;
-  static constexpr size_t bytes = sizeof(double) * 2 * NN + sizeof(float) * (6 * NN + 2 * MM + 64);
+  static constexpr size_t bytes = sizeof(double) * 2 * NN + sizeof(float) * (6 * NN + 3 * MM + 64);
 };
 
 template <int M>
 struct View2D {
   double *W;
-  float *Bh, *Bl, *Zh, *Zl, *Rf, *Tf, *Q, *I, *red;
+  float *Bh, *Bl, *Zh, *Zl, *Rf, *Tf, *Q, *I, *Qt, *red;
   __device__ explicit View2D(unsigned char *base) {
     constexpr int NN = Smem2D<M>::NN, MM = Smem2D<M>::MM;
     W = reinterpret_cast<double *>(base);
     float *f = reinterpret_cast<float *>(base + sizeof(double) * 2 * NN);
     Bh = f; Bl = f + NN; Zh = f + 2 * NN; Zl = f + 3 * NN; Rf = f + 4 * NN; Tf = f + 5 * NN;
-    Q = f + 6 * NN; I = Q + MM; red = I + MM;
+    Q = f + 6 * NN; I = Q + MM; Qt = I + MM; red = Qt + MM;
   }
   __device__ df64 z(int slot) const { return df64(Zh[slot], Zl[slot]); }
 };
@@ -249,7 +330,8 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
   __syncthreads();
   const df64 inv_scale = df64(1.0f, 0.0f) / scale;
   for (int round = 0; round < REFINE; ++round) {
-    fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
+    if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
+    else fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
     for (int s = threadIdx.x; s < NN; s += T2D) {
       const df64 zz = v.z(s) + scale * df64(v.Rf[s], 0.0f);
       v.Zh[s] = zz.hi;
@@ -318,7 +400,11 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   const df64 h2((float)N * 0.5f, 0.0f);          // 1 / (2 dx), exact
   const df64 dx(1.0 / N);
   const df64 scale = df64(4.0 / ((double)N * (double)N));   // 4 dx^2
-  for (int i = threadIdx.x; i < MM; i += T2D) { v.Q[i] = Qg[i]; v.I[i] = Ig[i]; }
+  for (int i = threadIdx.x; i < MM; i += T2D) {
+    v.Q[i] = Qg[i];
+    v.I[i] = Ig[i];
+    v.Qt[(i % M) * M + i / M] = Qg[i];
+  }
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) v.W[e] = src[e];
   __syncthreads();
   // b = D w_hat on every cell; moments of w_hat

@@ -179,7 +179,11 @@ k2d_frame_bwd(int B, int nt, const double *__restrict__ gw, const double *__rest
   const df64 h2((float)N * 0.5f, 0.0f);
   const df64 dx(1.0 / N);
   const df64 scale = df64(4.0 / ((double)N * (double)N));
-  for (int i = threadIdx.x; i < MM; i += T2D) { v.Q[i] = Qg[i]; v.I[i] = Ig[i]; }
+  for (int i = threadIdx.x; i < MM; i += T2D) {
+    v.Q[i] = Qg[i];
+    v.I[i] = Ig[i];
+    v.Qt[(i % M) * M + i / M] = Qg[i];
+  }
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) v.W[e] = gsrc[e];
   __syncthreads();
   df64 dot(0.0f, 0.0f), ww(0.0f, 0.0f);
