@@ -294,22 +294,22 @@ __device__ SliceResult newton2d(const Frame2D &F, Z2D &z, E2D &e, const SolverOp
   return R;
 }
 
-// Dynamic shared memory of one frame (N = 2M): w [2 N^2] double, then float arrays
-// b (hi, lo), z (hi, lo), r, t [4 M^2 = N^2 each], Q, inv, Q^T [M^2 each], reduction scratch.
+// Dynamic shared memory of one frame (N = 2M), float arrays: b (hi, lo), z (hi, lo), r, t
+// [4 M^2 = N^2 each], Q, inv, Q^T [M^2 each], reduction scratch (110.8 KB at M = 32: two
+// blocks per SM).  The frame's w_hat and w stay in global memory (L1 / L2): every pass reads
+// them from there.
 template <int M>
 struct Smem2D {
   static constexpr int N = 2 * M, NN = N * N, MM = M * M;
-  static constexpr size_t bytes = sizeof(double) * 2 * NN + sizeof(float) * (6 * NN + 3 * MM + 64);
+  static constexpr size_t bytes = sizeof(float) * (6 * NN + 3 * MM + 64);
 };
 
 template <int M>
 struct View2D {
-  double *W;
   float *Bh, *Bl, *Zh, *Zl, *Rf, *Tf, *Q, *I, *Qt, *red;
   __device__ explicit View2D(unsigned char *base) {
     constexpr int NN = Smem2D<M>::NN, MM = Smem2D<M>::MM;
-    W = reinterpret_cast<double *>(base);
-    float *f = reinterpret_cast<float *>(base + sizeof(double) * 2 * NN);
+    float *f = reinterpret_cast<float *>(base);
     Bh = f; Bl = f + NN; Zh = f + 2 * NN; Zl = f + 3 * NN; Rf = f + 4 * NN; Tf = f + 5 * NN;
     Q = f + 6 * NN; I = Q + MM; Qt = I + MM; red = Qt + MM;
   }
@@ -405,18 +405,17 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
     v.I[i] = Ig[i];
     v.Qt[(i % M) * M + i / M] = Qg[i];
   }
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) v.W[e] = src[e];
   __syncthreads();
   // b = D w_hat on every cell; moments of w_hat
   df64 a0(0.0f, 0.0f);
   float d2 = 0.0f, dinf = 0.0f;
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 x = dsplit(v.W[e]);
+    const df64 x = dsplit(src[e]);
     a0 = a0 + x * x;
   }
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
-    const df64 dv = div_at<M>(v.W, i, j, h2);
+    const df64 dv = div_at<M>(src, i, j, h2);
     const int s = cell_slot<M>(i, j);
     v.Bh[s] = dv.hi;
     v.Bl[s] = dv.lo;
@@ -434,7 +433,7 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
     const df64 y = divT_at<M>(v, e, h2);
     a2 = a2 + y * y;
     yinf = fabs_max(yinf, y.hi);
-    const df64 pw = dsplit(v.W[e]) - y;
+    const df64 pw = dsplit(src[e]) - y;
     pinf = fabs_max(pinf, pw.hi);
   }
   a0 = block_sumdf(a0, v.red);
@@ -471,7 +470,7 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   df64 w2(0.0f, 0.0f);
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
     const df64 y = divT_at<M>(v, e, h2);
-    const df64 x = dsplit(v.W[e]);
+    const df64 x = dsplit(src[e]);
     const df64 w = A * x + Cc * y;
     const double wd = df_to_double(w);
     dst[e] = wd;
@@ -480,7 +479,6 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
     const float dwv = (w - x).hi;
     obj = fmaf(dwv, dwv, obj);
     w2 = w2 + w * w;
-    v.W[e] = wd;
   }
   double *lb = lam_s + (size_t)f * NN;
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
@@ -491,7 +489,7 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   float hinf_all = 0.0f, hinf_act = 0.0f;
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
-    const float dv = div_at<M>(v.W, i, j, h2).hi;
+    const float dv = div_at<M>(dst, i, j, h2).hi;   // the written w (block-visible after the barrier)
     hinf_all = fabs_max(hinf_all, dv);
     if (!(i < 2 && j < 2)) hinf_act = fabs_max(hinf_act, dv);
   }

@@ -184,17 +184,16 @@ k2d_frame_bwd(int B, int nt, const double *__restrict__ gw, const double *__rest
     v.I[i] = Ig[i];
     v.Qt[(i % M) * M + i / M] = Qg[i];
   }
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) v.W[e] = gsrc[e];
   __syncthreads();
   df64 dot(0.0f, 0.0f), ww(0.0f, 0.0f);
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 x = dsplit(wsrc[e]), gx = dsplit(v.W[e]);
+    const df64 x = dsplit(wsrc[e]), gx = dsplit(gsrc[e]);
     dot = dot + x * gx;
     ww = ww + x * x;
   }
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
-    const df64 dv = div_at<M>(v.W, i, j, h2);
+    const df64 dv = div_at<M>(gsrc, i, j, h2);
     const int s = cell_slot<M>(i, j);
     v.Bh[s] = dv.hi;
     v.Bl[s] = dv.lo;
@@ -212,7 +211,7 @@ k2d_frame_bwd(int B, int nt, const double *__restrict__ gw, const double *__rest
   double *dst = gout + (size_t)fr * 2 * NN;
   for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
     const df64 y = divT_at<M>(v, e, h2);
-    const df64 a = (dsplit(v.W[e]) - y - bK * dx2 * dsplit(wsrc[e])) * ialpha;
+    const df64 a = (dsplit(gsrc[e]) - y - bK * dx2 * dsplit(wsrc[e])) * ialpha;
     dst[e] = bad ? NAN : df_to_double(a);
   }
   if (threadIdx.x == 0) {
