@@ -88,7 +88,10 @@ def test_double_float_ops_accuracy():
 def test_split_pair_exactness_and_range():
     rng = np.random.default_rng(1)
     x = rng.normal(size=5000) * np.exp(rng.uniform(-45, 35, size=5000))
-    x = np.concatenate([x, [0.0, -0.0, 1.0, -1.0, 2.0 ** -74, 2.0 ** 56, 1.999999999999, np.nextafter(2.0, 0)]])
+    ties = [1.0 + 2.0 ** -24, 1.0 + 3 * 2.0 ** -24, -(1.0 + 2.0 ** -24), 2.0 - 2.0 ** -25,
+            3.0 * (1.0 + 2.0 ** -24), 1.0 + 2.0 ** -24 + 2.0 ** -52]    # float ties and near-ties
+    x = np.concatenate([x, [0.0, -0.0, 1.0, -1.0, 2.0 ** -74, 2.0 ** 56, 1.999999999999,
+                            np.nextafter(2.0, 0)], ties])
     h = np.zeros(len(x), np.float32)
     l = np.zeros(len(x), np.float32)
     ok = np.zeros(len(x), np.int32)
