@@ -252,6 +252,30 @@ SNAP_API snap_status snap_constraint_residual(snap_problem_t p, int B, const dou
                                      void *workspace, size_t workspace_bytes,
                                      snap_stream_t stream);
 
+/* ---------------- the sampling loop around the projection ---------------- */
+
+/* Workspace of snap_pcfm_sample (device, 256-byte aligned). */
+SNAP_API snap_status snap_pcfm_workspace_size(snap_problem_t p, int B, size_t *bytes);
+
+/* One PCFM sampling pass of the three-step variant (Sampling section, Eqs. 1-3): for
+ * tau = k / n_steps, k = 0 .. n_steps-1: forward shoot u_hat_1 = u_tau + (1 - tau) v,
+ * projection u_1 = argmin 1/2 ||u - u_hat_1||^2 s.t. h(u; params) = 0 (snap_project's
+ * forward path, start u_hat_1), OT pull-back u_tau' = u_0 + tau' (u_1 - u_0).  The flow
+ * model is replaced by the analytic velocity v(u, tau) = (x1 - u_0) + sigma0 (1 - tau) xi
+ * (the straight-path OT velocity from the prior sample u_0 to the data sample x1, plus a
+ * decaying perturbation along xi).
+ *   u0, x1, xi: device [B][n_vars] (16-byte aligned); params as snap_project.
+ *   u: device [B][n_vars] out: u_1 of the last step (= the sample at tau = 1); it also holds
+ *   the running u_1 between steps.  lambda, stats: of the last projection.
+ * Asynchronous on stream, no allocation or synchronisation (capturable in a CUDA graph).
+ * Errors: as snap_project; INVALID_ARG for n_steps outside [1, 100000] or a NaN sigma0. */
+SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, double sigma0,
+                                      const double *u0, const double *x1, const double *xi,
+                                      const double *params, double *u, double *lambda,
+                                      snap_stats *stats, const snap_options *opt,
+                                      void *workspace, size_t workspace_bytes,
+                                      snap_stream_t stream);
+
 /* ---------------- forward projection without any allocation ---------------- */
 
 /* Bytes of the library's static device scratch used by snap_project_noalloc (8 MiB). */

@@ -65,6 +65,9 @@ _PROTOS = {
     "snap_project_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         _vp, C.c_size_t, _vp]),
     "snap_constraint_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
+    "snap_pcfm_workspace_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
+    "snap_pcfm_sample": (C.c_int, [_vp, C.c_int, C.c_int, C.c_double, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   _vp, C.POINTER(Options), _vp, C.c_size_t, _vp]),
     "snap_project_noalloc": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.POINTER(Options), _vp]),
     "snap_batch_create": (C.c_int, [C.c_int, C.POINTER(_vp), C.c_int, _ip, C.POINTER(_vp)]),
     "snap_batch_destroy": (None, [_vp]),

@@ -155,6 +155,33 @@ class Problem:
                                          _ptr(lam), _ptr(st), C.byref(o), _stream(stream)))
         return u, lam, st
 
+    def pcfm_sample(self, u0, x1, xi, params, n_steps, sigma0=0.0, opts=None, out=None,
+                    stream=None):
+        """snap_pcfm_sample: one sampling pass of n_steps shoot / project / pull-back steps
+        with the analytic velocity (x1 - u0) + sigma0 (1 - tau) xi.  Returns (u, lambda,
+        stats) of the last projection."""
+        B = u0.shape[0]
+        self._check_dev(u0, x1, xi, params)
+        dev = u0.device
+        if out is None:
+            u = torch.empty_like(u0)
+            lam = torch.empty(B, self.n_rows, dtype=torch.float64, device=dev)
+            st = torch.empty(B, 40, dtype=torch.uint8, device=dev)
+        else:
+            u, lam, st = out
+        key = ("pcfm", B, str(dev))
+        ws = self._ws.get(key)
+        if ws is None:
+            n = C.c_size_t()
+            check(lib().snap_pcfm_workspace_size(self._h, B, C.byref(n)))
+            ws = torch.empty(max(n.value, 8), dtype=torch.uint8, device=dev)
+            self._ws[key] = ws
+        o = opts if opts is not None else options()
+        check(lib().snap_pcfm_sample(self._h, B, int(n_steps), float(sigma0), _ptr(u0), _ptr(x1),
+                                     _ptr(xi), _ptr(params), _ptr(u), _ptr(lam), _ptr(st),
+                                     C.byref(o), _ptr(ws), ws.numel(), _stream(stream)))
+        return u, lam, st
+
     def backward(self, grad_u, u, lam, params, stats=None, cache=None, stream=None,
                  with_params=True):
         B = u.shape[0]

@@ -161,6 +161,8 @@ size_t ws_bytes(const snap_problem *p, int B) {
 
 void snap_note_launch(int n) { g_launches += n; }
 
+void snap_reset_launches() { g_launches = 0; }
+
 snap_status snap_fail_msg(snap_status st, const char *msg) { return fail(st, "%s", msg); }
 
 snap_status snap_check_options(const snap_options &o) { return check_opts(o); }

@@ -96,6 +96,7 @@ snap_status snap_check_options(const snap_options &o);
 
 // Kernel-launch bookkeeping (per host thread) and optional event timing (snap_profile.cu).
 void snap_note_launch(int n);
+void snap_reset_launches();
 int snap_prof_begin(cudaStream_t s, const char *name);
 void snap_prof_end(cudaStream_t s, int id);
 

@@ -106,10 +106,22 @@ def gen_uneven(seed=1004, n_inst=1024, frac_1d=0.75, n2d=32, nt2d=8):
     return out
 
 
+def gen_pcfm(seed, B, nx, nt, family="B"):
+    """Inputs of one PCFM sampling pass on a 1-D family: the data sample x1 and the
+    parameters from gen_1d (seed), the prior sample u0 ~ N(0, 1) and the perturbation
+    direction xi ~ N(0, 1) (seed + 1)."""
+    x1, pr = gen_1d(seed, B, nx, nt, family)
+    rng = np.random.default_rng(seed + 1)
+    u0 = rng.normal(size=(B, nt * nx))
+    xi = rng.normal(size=(B, nt * nx))
+    return u0, x1.reshape(B, -1), xi, pr
+
+
 WORKLOADS = {
     "small_1d": dict(family="A", B=8, nx=32, nt=32, seed=1000),
     "burgers_1d": dict(family="B", B=512, nx=128, nt=100, seed=1001),
     "adjoint_1d": dict(family="B", B=512, nx=128, nt=100, seed=1001, gbar_seed=1002),
     "div_2d": dict(family="C", B=64, N=64, nt=16, seed=1003),
     "uneven": dict(n_inst=1024, seed=1004),
+    "pcfm_1d": dict(family="B", B=512, nx=128, nt=100, seed=1005, n_steps=10, sigma0=0.3),
 }
