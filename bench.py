@@ -47,9 +47,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the 2-D and uneven-batch measurements reported beside the headline")
+                    help="skip the 2-D, uneven-batch and sampling-loop measurements beside the headline")
     ap.add_argument("--extra-only", action="store_true",
-                    help="run only the 2-D and uneven-batch measurements (one JSON line)")
+                    help="run only the 2-D, uneven-batch and sampling-loop measurements (one JSON line)")
     return ap.parse_args()
 
 
@@ -211,8 +211,8 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     if args.extra_only:
         hbm0 = measured_peaks().get("hbm_gbs") or 6400.0
-        print(json.dumps({"div_2d": measure_div2d(dev, hbm0), "uneven": measure_uneven(dev)}),
-              flush=True)
+        print(json.dumps({"div_2d": measure_div2d(dev, hbm0), "uneven": measure_uneven(dev),
+                          "pcfm": measure_pcfm(dev)}), flush=True)
         return 0
     w = WORKLOAD
     B, nx, nt = w["B"], w["nx"], w["nt"]
@@ -397,6 +397,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_extra:
         extra["div_2d"] = measure_div2d(dev, hbm)
         extra["uneven"] = measure_uneven(dev)
+        extra["pcfm"] = measure_pcfm(dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -574,6 +575,52 @@ def measure_uneven(dev, reps=30):
             "makespan_us": makespan_us, "input_bytes": in_bytes,
             "persistent_launches_per_call": 1,
             "grouped_launches_per_call": sum(2 if f == "C" else 3 for f, _, _ in keys)}
+
+
+def measure_pcfm(dev, reps=20):
+    """The sampling loop: one PCFM pass (10 shoot / project / pull-back steps) over B = 512
+    Burgers samples, captured in one CUDA graph; two rotating input sets (> L2)."""
+    import torch
+
+    from paper_2607_00095_b300 import Problem, decode_stats, synthetic
+    w = synthetic.WORKLOADS["pcfm_1d"]
+    B, nx, nt, N, s0 = w["B"], w["nx"], w["nt"], w["n_steps"], w["sigma0"]
+    p = Problem(w["family"], nx, nt)
+    sets = []
+    for r in range(2):
+        u0, x1, xi, pr = synthetic.gen_pcfm(w["seed"] + 7919 * r, B, nx, nt, w["family"])
+        d = [torch.as_tensor(a, device=dev) for a in (u0, x1, xi, pr)]
+        out = (torch.empty_like(d[0]), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        p.pcfm_sample(*d, n_steps=N, sigma0=s0, out=out)
+        sets.append((d, out))
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(cap):
+        for d, out in sets:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                p.pcfm_sample(*d, n_steps=N, sigma0=s0, out=out, stream=cap)
+            graphs.append(g)
+    for g in graphs:
+        g.replay()
+    it = [0]
+
+    def step():
+        graphs[it[0] % 2].replay()
+        it[0] += 1
+    ms = _event_ms(step, reps)
+    conv = 0
+    for d, out in sets:
+        _, hinf = p.residual(out[0], d[3], want_rows=False)
+        st = decode_stats(out[2])
+        conv += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+    conv /= 2
+    return {"workload": "pcfm_1d", "B": B, "nx": nx, "nt": nt, "n_steps": N, "sigma0": s0,
+            "ms_per_pass": ms, "converged_samples_per_pass": conv,
+            "samples_per_s": conv / (ms / 1e3), "projections_per_s": B * N / (ms / 1e3),
+            "velocity": "analytic: (x1 - u0) + sigma0 (1 - tau) xi"}
 
 
 def lib_project_cache(p, d_uh, d_pr, opts, out, cache, ws):
