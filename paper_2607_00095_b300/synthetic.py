@@ -15,6 +15,8 @@ Workloads (name -> sizes):
   div_2d      family C, B=64,  N=64,   nt=16   (divergence + kinetic energy), seed 1003
   uneven      1024 instances: 75 % family B with nx in {64,96,128,192,256},
               nt in {50,100,200}; 25 % family C at 32x32x8; seed 1004
+  pcfm_1d     burgers_1d shapes: data sample x1 = gen_1d's u_hat (seed 1005), prior sample
+              u0 and perturbation xi ~ N(0, 1) (seed 1006), 10 steps, sigma0 = 0.3
 """
 import numpy as np
 
