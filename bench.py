@@ -53,6 +53,24 @@ def parse():
     return ap.parse_args()
 
 
+def shard_seed(seed, r, rank):
+    """Seed of rotation set r on rank `rank`: every rank projects its own samples (weak
+    scaling; the batches of different ranks are independent problems)."""
+    return seed + 7919 * r + 104729 * rank
+
+
+def reduce_over_ranks(elapsed_ms, converged, device):
+    """Whole-job timing and count over all ranks: the slowest rank's time, the sum of the
+    converged samples (one all-reduce each; nothing on the data path)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(converged)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -223,7 +241,7 @@ def run_ours(args, rank, world, local):
     sets = []
     host0 = None
     for r in range(ROTATE):
-        seed = w["seed"] + 7919 * r + 104729 * rank
+        seed = shard_seed(w["seed"], r, rank)
         uh, pr = synthetic.gen_1d(seed, B, nx, nt, w["family"])
         if r == 0:
             host0 = (uh, pr)
@@ -311,13 +329,7 @@ def run_ours(args, rank, world, local):
         conv_per_set.append(int(ok.sum()))
     conv = sum(conv_per_set[i % ROTATE] for i in range(steps_timed))
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-        c = torch.tensor([conv], dtype=torch.float64, device=dev)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        conv = int(c.item())
+        elapsed_ms, conv = reduce_over_ranks(elapsed_ms, conv, dev)
     value = conv / (elapsed_ms / 1e3)
 
     # adjoint / forward time (differentiation workload: same shapes, dL/du ~ N(0, 1))
