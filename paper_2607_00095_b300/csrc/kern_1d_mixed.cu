@@ -106,7 +106,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
           // the IC slice is handled by the per-sample prepare kernel
         } else {
           // CH independent 16-byte loads in flight per lane, then the accumulation
-          constexpr int CH = 8;
+          constexpr int CH = 16;
           for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
             double2 v[CH];
 #pragma unroll
@@ -341,7 +341,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
       const double *row = uh + (size_t)s2 * nx;
       double *out = u + (size_t)s2 * nx;
       if (kd == KIND_MOMENT) {
-        constexpr int CH = 8;
+        constexpr int CH = 16;
         for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
           double2 v[CH];
 #pragma unroll
