@@ -91,7 +91,7 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
       if (s < total && (s % g.nt) != 0) {
         const double *urow = u + (size_t)s * nx;
         const double *grow = gu + (size_t)s * nx;
-        constexpr int CH = 4;
+        constexpr int CH = 8;
         for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
           double2 vu[CH], vg[CH];
 #pragma unroll
@@ -284,7 +284,7 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
       const double *urow = u + (size_t)s2 * nx;
       const double *grow = gu + (size_t)s2 * nx;
       double *out = gh + (size_t)s2 * nx;
-      constexpr int CH = 4;
+      constexpr int CH = 8;
       for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
         double2 vu[CH], vg[CH];
 #pragma unroll

@@ -62,7 +62,7 @@ __device__ __forceinline__ df64 shfl_df(df64 v, int off) {
   return df64(__shfl_xor_sync(FULL, v.hi, off), __shfl_xor_sync(FULL, v.lo, off));
 }
 
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(64, 8)
 k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
           const SampleDerived *__restrict__ sd, double *__restrict__ u,
           double *__restrict__ lam, BlockStat *__restrict__ bst,
@@ -370,12 +370,12 @@ void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *
                      const SampleDerived *sd, double *u, double *lambda, BlockStat *bst,
                      SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s) {
   const long long ntiles = ((long long)B * g.nt + 31) / 32;
-  long long blocks = (ntiles + 3) / 4;
+  long long blocks = (ntiles + 1) / 2;
   if (blocks_per_sm > 0 && blocks > 148LL * blocks_per_sm) blocks = 148LL * blocks_per_sm;
-  if (blocks > 148LL * 64) blocks = 148LL * 64;
+  if (blocks > 148LL * 128) blocks = 148LL * 128;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3(128);
+  cfg.blockDim = dim3(64);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
