@@ -65,7 +65,8 @@ struct SliceOptsT {
 template <class T>
 DF_INL T sl_abs(T x) { return x < T(0) ? -x : x; }
 
-// 1/x: exact division in FP64, the IEEE-rounded reciprocal in float, the double-float
+// 1/x: exact division in FP64, the hardware reciprocal approximation in float (df_rcp; the
+// float phase is a predictor whose steps are refined in double-float), the double-float
 // quotient in df64
 DF_INL double sl_rcp(double x) { return 1.0 / x; }
 DF_INL float sl_rcp(float x) { return df_rcp(x); }
