@@ -230,7 +230,8 @@ def run_ours(args, rank, world, local):
     if args.extra_only:
         hbm0 = measured_peaks().get("hbm_gbs") or 6400.0
         print(json.dumps({"div_2d": measure_div2d(dev, hbm0), "uneven": measure_uneven(dev),
-                          "pcfm": measure_pcfm(dev)}), flush=True)
+                          "pcfm": measure_pcfm(dev),
+                          "vorticity_2d": measure_vorticity(dev, hbm0)}), flush=True)
         return 0
     w = WORKLOAD
     B, nx, nt = w["B"], w["nx"], w["nt"]
@@ -435,6 +436,7 @@ def run_ours(args, rank, world, local):
         extra["div_2d"] = measure_div2d(dev, hbm)
         extra["uneven"] = measure_uneven(dev)
         extra["pcfm"] = measure_pcfm(dev)
+        extra["vorticity_2d"] = measure_vorticity(dev, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -612,6 +614,57 @@ def measure_uneven(dev, reps=30):
             "makespan_us": makespan_us, "input_bytes": in_bytes,
             "persistent_launches_per_call": 1,
             "grouped_launches_per_call": sum(2 if f == "C" else 3 for f, _, _ in keys)}
+
+
+def measure_vorticity(dev, hbm, reps=50):
+    """The 2-D vorticity constraints of the Navier-Stokes problem (IC, total vorticity,
+    enstrophy per frame): B = 512 samples of 16 x 16 x 50 frames; four rotating sets (> L2),
+    CUDA graphs."""
+    import torch
+
+    from paper_2607_00095_b300 import api, decode_stats, synthetic, vorticity_problem
+    w = synthetic.WORKLOADS["vorticity_2d"]
+    B, N, nt = w["B"], w["N"], w["nt"]
+    p = vorticity_problem(N, nt)
+    sets = []
+    for r in range(4):
+        uh, pr = synthetic.gen_vorticity(w["seed"] + 7919 * r, B, N, nt)
+        d_uh = torch.as_tensor(uh.reshape(B, -1), device=dev)
+        d_pr = torch.as_tensor(pr, device=dev)
+        out = (torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        sets.append((d_uh, d_pr, out))
+    ws = p.workspace(B, dev)
+    for d_uh, d_pr, out in sets:
+        p.project(d_uh, d_pr, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    cap = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(cap):
+        for d_uh, d_pr, out in sets:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                p.project(d_uh, d_pr, out=out, workspace=ws, stream=cap)
+            graphs.append(g)
+    for g in graphs:
+        g.replay()
+    it = [0]
+
+    def step():
+        graphs[it[0] % 4].replay()
+        it[0] += 1
+    ms = _event_ms(step, reps)
+    conv = 0
+    for d_uh, d_pr, out in sets:
+        _, hinf = p.residual(out[0], d_pr, want_rows=False)
+        st = decode_stats(out[2])
+        conv += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+    conv /= 4
+    bytes_per_call = (8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40) * B
+    return {"workload": "vorticity_2d", "B": B, "N": N, "nt": nt, "ms_per_call": ms,
+            "converged_per_call": conv, "projections_per_s": conv / (ms / 1e3),
+            "hbm_frac_of_measured_step": bytes_per_call / (ms / 1e3) / 1e9 / hbm,
+            "path": "family A rows on flattened frames (nx = N^2), mixed-pipe tile kernel"}
 
 
 def measure_pcfm(dev, reps=20):

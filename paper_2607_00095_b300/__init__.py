@@ -5,4 +5,5 @@
 The compute path is libsnap.so (hand-written sm_103a CUDA behind the C ABI of include/snap.h);
 importing this package does not load it, the first call does, and fails loudly if it is missing.
 """
-from .api import Batch, Problem, SnapProject, decode_stats, measure_fp64_rate, options, project  # noqa: F401
+from .api import (Batch, Problem, SnapProject, decode_stats, measure_fp64_rate, options,  # noqa: F401
+                  project, vorticity_problem)

@@ -207,6 +207,19 @@ class Problem:
         return h, hinf
 
 
+# energy_floor that switches the floor of the energy targets off: E_k = E0 exp(-r t_k)
+NO_ENERGY_FLOOR = -1e300
+
+
+def vorticity_problem(N, nt, max_batch=0):
+    """The 2-D vorticity constraints of the Navier-Stokes problem (Appendix A): per frame of the
+    N x N periodic grid on [0, 1]^2, the IC frame w(., 0) = w_IC, total vorticity
+    int w = int w_IC and enstrophy int w^2 = int w_IC^2.  With a frame flattened to N^2 values
+    and dx dy = 1 / N^2 these are exactly the rows of family A with nx = N^2, rate 0 and no
+    energy floor; params = [w_IC (N^2 values), 0.0]."""
+    return Problem("A", N * N, nt, energy_floor=NO_ENERGY_FLOOR, max_batch=max_batch)
+
+
 class SnapProject(torch.autograd.Function):
     """u = projection(u_hat; params) with the implicit-function adjoint as backward.
 

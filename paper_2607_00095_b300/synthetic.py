@@ -17,6 +17,7 @@ Workloads (name -> sizes):
               nt in {50,100,200}; 25 % family C at 32x32x8; seed 1004
   pcfm_1d     burgers_1d shapes: data sample x1 = gen_1d's u_hat (seed 1005), prior sample
               u0 and perturbation xi ~ N(0, 1) (seed 1006), 10 steps, sigma0 = 0.3
+  vorticity_2d  2-D vorticity (IC, total vorticity, enstrophy), B=512, 16x16, nt=50, seed 1007
 """
 import numpy as np
 
@@ -108,6 +109,31 @@ def gen_uneven(seed=1004, n_inst=1024, frac_1d=0.75, n2d=32, nt2d=8):
     return out
 
 
+def gen_vorticity(seed, B, N, nt, noise=0.1, decay=0.02, alpha=2.5, tau=7.0):
+    """2-D vorticity frames on a periodic N x N grid of [0, 1]^2, nt frames, flattened to
+    N^2 values per frame (row j, column i at j N + i).  Per sample: an initial vorticity w_IC
+    from a Gaussian random field with spectral amplitude (4 pi^2 |k|^2 + tau^2)^(-alpha/2)
+    (zero mean, scaled to unit rms); candidate frames u_hat(t_k) = w_IC (1 - decay t_k) +
+    N(0, noise^2) i.i.d. with t_k = k / (nt - 1).  params[b] = [w_IC (N^2 values), 0.0] (the
+    family-A layout: IC values, then rate 0: total vorticity and enstrophy conserved).
+    Returns (u_hat [B, nt, N^2], params [B, N^2 + 1])."""
+    rng = np.random.default_rng(seed)
+    k = np.fft.fftfreq(N, d=1.0 / N)
+    k2 = k[None, :] ** 2 + k[:, None] ** 2
+    amp = (4.0 * np.pi ** 2 * k2 + tau ** 2) ** (-alpha / 2.0)
+    amp[0, 0] = 0.0
+    t = np.arange(nt) / (nt - 1)
+    u_hat = np.empty((B, nt, N * N))
+    params = np.zeros((B, N * N + 1))
+    for b in range(B):
+        spec = amp * (rng.normal(size=(N, N)) + 1j * rng.normal(size=(N, N)))
+        w = np.real(np.fft.ifft2(spec))
+        w = w / np.sqrt(np.mean(w * w))
+        params[b, :N * N] = w.ravel()
+        u_hat[b] = w.ravel()[None, :] * (1.0 - decay * t)[:, None] + rng.normal(0.0, noise, size=(nt, N * N))
+    return np.ascontiguousarray(u_hat), params
+
+
 def gen_pcfm(seed, B, nx, nt, family="B"):
     """Inputs of one PCFM sampling pass on a 1-D family: the data sample x1 and the
     parameters from gen_1d (seed), the prior sample u0 ~ N(0, 1) and the perturbation
@@ -126,4 +152,5 @@ WORKLOADS = {
     "div_2d": dict(family="C", B=64, N=64, nt=16, seed=1003),
     "uneven": dict(n_inst=1024, seed=1004),
     "pcfm_1d": dict(family="B", B=512, nx=128, nt=100, seed=1005, n_steps=10, sigma0=0.3),
+    "vorticity_2d": dict(B=512, N=16, nt=50, seed=1007),
 }
