@@ -86,7 +86,14 @@ typedef enum {
   SNAP_FAMILY_C_DIV_ENERGY = 2,
   /* Appendix C worked example (IC + left-Riemann mass differences).  Pattern queries
    * only; snap_project returns SNAP_ERR_UNSUPPORTED for it. */
-  SNAP_FAMILY_TOY_LEFT_RIEMANN = 3
+  SNAP_FAMILY_TOY_LEFT_RIEMANN = 3,
+  /* Boundary-condition regime of the Burgers problem (Appendix A; discretisation of
+   * Appendix D): 1-D field on [0, 1], x_i = i dx, dx = 1 / (nx - 1), per slice k the
+   * Dirichlet row u_{k,0} = u_L, the mass row dx sum_i u_{k,i} = m0 and the Neumann row
+   * u_{k,nx-1} = u_{k,nx-2}.  params[b] = {u_L, m0}; rows grouped by type (nt Dirichlet, nt
+   * mass, nt Neumann); nx in [4, 65536] (any parity), desc.rows must be 0.  Linear rows:
+   * one Newton step; snap_project_backward returns SNAP_ERR_UNSUPPORTED for it. */
+  SNAP_FAMILY_D_BURGERS_BC = 4
 } snap_family;
 
 /* Row-type bits for snap_problem_desc.rows (1-D families). */

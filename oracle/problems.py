@@ -38,9 +38,10 @@ from dataclasses import dataclass, field
 import numpy as np
 
 ROW_IC, ROW_MASS, ROW_ENERGY, ROW_BOUNDARY, ROW_DIV, ROW_KE, ROW_TOYMASS = range(7)
+ROW_DIRICHLET, ROW_NEUMANN = 7, 8
 ROW_TYPE_NAMES = {ROW_IC: "ic", ROW_MASS: "mass", ROW_ENERGY: "energy",
                   ROW_BOUNDARY: "boundary", ROW_DIV: "div", ROW_KE: "kinetic_energy",
-                  ROW_TOYMASS: "mass"}
+                  ROW_TOYMASS: "mass", ROW_DIRICHLET: "dirichlet", ROW_NEUMANN: "neumann"}
 
 
 @dataclass
@@ -188,6 +189,38 @@ def grad_params_1d(family, nx, nt, params, badj, energy_floor=0.05):
 # ----------------------------------------------------------------------------------------
 
 DROPPED_CELLS_2D = ((0, 0), (1, 0), (0, 1), (1, 1))     # (i, j), one per parity class
+
+
+def structure_bc(nx, nt):
+    """Boundary-condition regime of the Burgers problem (Appendix A, discretisation of
+    Appendix D): x_i = i dx on [0, 1], dx = 1 / (nx - 1); per slice k a Dirichlet row
+    u_{k,0} - u_L, a mass row dx sum_i u_{k,i} - m0 (Riemann sum) and a Neumann row
+    u_{k,nx-1} - u_{k,nx-2}; rows grouped by type, all active."""
+    assert nx >= 4 and nt >= 1
+    dx = 1.0 / (nx - 1)
+    empty = ([], [])
+    arows, qrows, types = [], [], []
+    for k in range(nt):
+        arows.append(([k * nx], [1.0])); qrows.append(empty); types.append(ROW_DIRICHLET)
+    for k in range(nt):
+        arows.append((list(range(k * nx, (k + 1) * nx)), [dx] * nx)); qrows.append(empty)
+        types.append(ROW_MASS)
+    for k in range(nt):
+        arows.append(([k * nx + nx - 2, k * nx + nx - 1], [-1.0, 1.0])); qrows.append(empty)
+        types.append(ROW_NEUMANN)
+    m = len(types)
+    ap, ac, av = _csr(arows, m)
+    qp, qc, qv = _csr(qrows, m)
+    return Structure("D", nx * nt, m, ap, ac, av, qp, qc, qv, np.ones(m, np.uint8),
+                     np.asarray(types, np.int32), dict(nx=nx, nt=nt))
+
+
+def rhs_bc(nx, nt, params):
+    """b for every row: params [B, 2] = (u_L, m0) -> b [B, 3 nt]."""
+    params = np.atleast_2d(np.asarray(params, np.float64))
+    Bn = params.shape[0]
+    return np.concatenate([np.repeat(params[:, 0:1], nt, axis=1),
+                           np.repeat(params[:, 1:2], nt, axis=1), np.zeros((Bn, nt))], axis=1)
 
 
 def structure_2d(N, nt):

@@ -9,7 +9,7 @@ SNAP_OK = 0
 NOALLOC_SCRATCH_BYTES = 8388608
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NO_MEMORY",
                 5: "WORKSPACE", 6: "NOT_READY"}
-FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY = 0, 1, 2, 3
+FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY, FAMILY_D = 0, 1, 2, 3, 4
 ROW_IC, ROW_MASS, ROW_ENERGY, ROW_BOUNDARY = 1, 2, 4, 8
 PATH_AUTO, PATH_GENERAL, PATH_MOMENT, PATH_MIXED = 0, 1, 2, 3
 SAMPLE_STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH", 3: "NONFINITE", 4: "INFEASIBLE_PARAMS",

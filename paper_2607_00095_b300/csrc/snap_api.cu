@@ -107,6 +107,30 @@ void build_pattern_toy(snap_problem *p, int nx, int nt) {
   p->info.n_rows_nominal = m;
 }
 
+// Family D: per slice a Dirichlet row (x_0), then the mass rows, then the Neumann rows
+// (x_{nx-2}, x_{nx-1}); grouped by type: D rows 0..nt-1, M rows nt..2nt-1, N rows 2nt..3nt-1.
+void build_pattern_bc(snap_problem *p, int nx, int nt) {
+  std::vector<int> rp(1, 0), ci;
+  for (int k = 0; k < nt; ++k) { ci.push_back(k * nx); rp.push_back((int)ci.size()); }
+  for (int k = 0; k < nt; ++k) {
+    for (int i = 0; i < nx; ++i) ci.push_back(k * nx + i);
+    rp.push_back((int)ci.size());
+  }
+  for (int k = 0; k < nt; ++k) {
+    ci.push_back(k * nx + nx - 2); ci.push_back(k * nx + nx - 1);
+    rp.push_back((int)ci.size());
+  }
+  const int m = (int)rp.size() - 1;
+  p->row_ptr = (int *)malloc(sizeof(int) * rp.size());
+  p->col_idx = (int *)malloc(sizeof(int) * (ci.size() + 1));
+  p->active = (unsigned char *)malloc(m + 1);
+  memcpy(p->row_ptr, rp.data(), sizeof(int) * rp.size());
+  memcpy(p->col_idx, ci.data(), sizeof(int) * ci.size());
+  memset(p->active, 1, m);
+  p->info.pattern_nnz = (long long)ci.size();
+  p->info.n_rows_active = m;
+}
+
 // 2-D family C: divergence rows [f][j][i] (4 stencil columns), then one energy row per frame.
 void build_pattern_2d(snap_problem *p, int N, int nt) {
   std::vector<int> rp(1, 0), ci;
@@ -154,6 +178,7 @@ snap_status check_batch(const snap_problem *p, int B) {
 
 size_t ws_bytes(const snap_problem *p, int B) {
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) return ws_bytes_2d(p, B);
+  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) return ws_bytes_1dbc(p, B);
   return ws_bytes_1d(p, B);
 }
 
@@ -267,6 +292,18 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
       }
       break;
     }
+    case SNAP_FAMILY_D_BURGERS_BC: {
+      if (d->nx < 4 || d->nx > 65536 || d->rows != 0) {
+        free(p);
+        return fail(SNAP_ERR_INVALID_ARG, "family D: nx must be in [4, 65536] and rows 0");
+      }
+      p->info.n_vars = d->nx * d->nt;
+      p->info.n_rows_nominal = 3 * d->nt;
+      p->info.n_params = 2;
+      p->info.n_blocks = d->nt;
+      build_pattern_bc(p, d->nx, d->nt);
+      break;
+    }
     case SNAP_FAMILY_TOY_LEFT_RIEMANN: {
       if (d->nx < 2 || d->nx > 4096) {
         free(p);
@@ -328,7 +365,8 @@ snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes) {
   snap_status st = check_batch(p, B);
   if (st != SNAP_OK) return st;
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) *bytes = cache_bytes_2d(p, B);
-  else if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN) *bytes = 0;
+  else if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN ||
+           p->desc.family == SNAP_FAMILY_D_BURGERS_BC) *bytes = 0;
   else *bytes = sizeof(SliceFactor) * (size_t)B * p->g1.nt;
   return SNAP_OK;
 }
@@ -364,7 +402,11 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
   if (u0 == u_hat) u0 = nullptr;
   const SolverOpts so = to_solver(o);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
+  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) {
+    if (u0) return fail(SNAP_ERR_UNSUPPORTED, "family D starts at u_hat (linear rows: one step)");
+    e = launch_1dbc_forward(p, B, u_hat, params, u, lambda, stats, so, workspace,
+                            (cudaStream_t)stream);
+  } else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_forward(p, B, u_hat, params, u0, u, lambda, stats, adjoint_cache, so, path,
                           workspace, (cudaStream_t)stream);
   else
@@ -386,6 +428,8 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
   if (st != SNAP_OK) return st;
   if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN)
     return fail(SNAP_ERR_UNSUPPORTED, "the toy family supports pattern queries only");
+  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
+    return fail(SNAP_ERR_UNSUPPORTED, "no adjoint for family D in this build");
   if (B == 0) return SNAP_OK;
   if (!grad_u || !u || !lambda || !params || !grad_u_hat)
     return fail(SNAP_ERR_INVALID_ARG, "null grad_u / u / lambda / params / grad_u_hat");
@@ -421,7 +465,9 @@ snap_status snap_constraint_residual(snap_problem_t p, int B, const double *u,
   if (!workspace || workspace_bytes < need)
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
+  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
+    e = launch_1dbc_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
   else
     e = launch_1d_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);

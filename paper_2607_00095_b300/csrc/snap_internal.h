@@ -141,5 +141,15 @@ void launch_finalize_stats(int B, int nblk, const BlockStat *bst, double tol_h, 
                            cudaStream_t s);
 size_t cache_bytes_2d(const snap_problem *p, int B);
 
+// Family D (kern_1dbc.cu).
+size_t ws_bytes_1dbc(const snap_problem *p, int B);
+cudaError_t launch_1dbc_forward(const snap_problem *p, int B, const double *u_hat,
+                                const double *params, double *u, double *lambda,
+                                snap_stats *stats, const SolverOpts &o, void *ws,
+                                cudaStream_t s);
+cudaError_t launch_1dbc_residual(const snap_problem *p, int B, const double *u,
+                                 const double *params, double *h, double *h_inf, void *ws,
+                                 cudaStream_t s);
+
 // Alignment helper for workspace carving.
 inline size_t snap_align256(size_t x) { return (x + 255) & ~(size_t)255; }

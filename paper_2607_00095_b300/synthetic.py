@@ -18,6 +18,7 @@ Workloads (name -> sizes):
   pcfm_1d     burgers_1d shapes: data sample x1 = gen_1d's u_hat (seed 1005), prior sample
               u0 and perturbation xi ~ N(0, 1) (seed 1006), 10 steps, sigma0 = 0.3
   vorticity_2d  2-D vorticity (IC, total vorticity, enstrophy), B=512, 16x16, nt=50, seed 1007
+  burgers_bc_1d  family D (Dirichlet, mass, Neumann per slice), B=512, nx=nt=101, seed 1008
 """
 import numpy as np
 
@@ -134,6 +135,26 @@ def gen_vorticity(seed, B, N, nt, noise=0.1, decay=0.02, alpha=2.5, tau=7.0):
     return np.ascontiguousarray(u_hat), params
 
 
+def gen_burgers_bc(seed, B, nx, nt, noise=0.1, eps=0.02):
+    """Boundary-condition regime of the Burgers problem on [0, 1] (x_i = i / (nx - 1)),
+    t_k = k / (nt - 1): per sample a front u_IC(x) = 1 / (1 + exp((x - p_loc) / eps)) with
+    p_loc ~ U(0.2, 0.8), travelling at speed 1/2 (the inviscid Burgers shock speed between 1
+    and 0), u_hat = u_IC(x - t / 2) + N(0, noise^2); params = [u_L, m0] with u_L ~ U(0, 1)
+    and m0 = dx sum_i u_IC(x_i) (the mass of the initial profile, Riemann sum).
+    Returns (u_hat [B, nt, nx], params [B, 2])."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) / (nx - 1)
+    t = np.arange(nt) / (nt - 1)
+    dx = 1.0 / (nx - 1)
+    p_loc = rng.uniform(0.2, 0.8, size=B)
+    u_l = rng.uniform(0.0, 1.0, size=B)
+    xx = x[None, None, :] - 0.5 * t[None, :, None] - p_loc[:, None, None]
+    u_hat = 1.0 / (1.0 + np.exp(np.clip(xx / eps, -700, 700))) + rng.normal(0.0, noise, size=(B, nt, nx))
+    u_ic = 1.0 / (1.0 + np.exp(np.clip((x[None, :] - p_loc[:, None]) / eps, -700, 700)))
+    params = np.stack([u_l, dx * u_ic.sum(axis=1)], axis=1)
+    return np.ascontiguousarray(u_hat), np.ascontiguousarray(params)
+
+
 def gen_pcfm(seed, B, nx, nt, family="B"):
     """Inputs of one PCFM sampling pass on a 1-D family: the data sample x1 and the
     parameters from gen_1d (seed), the prior sample u0 ~ N(0, 1) and the perturbation
@@ -153,4 +174,5 @@ WORKLOADS = {
     "uneven": dict(n_inst=1024, seed=1004),
     "pcfm_1d": dict(family="B", B=512, nx=128, nt=100, seed=1005, n_steps=10, sigma0=0.3),
     "vorticity_2d": dict(B=512, N=16, nt=50, seed=1007),
+    "burgers_bc_1d": dict(B=512, nx=101, nt=101, seed=1008),
 }
