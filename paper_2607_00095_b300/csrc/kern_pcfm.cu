@@ -17,13 +17,27 @@
 
 namespace {
 
-// u_hat_1 for step tau; first = (tau == 0): u_tau = u_0 and u_1 is not read.
+__device__ __forceinline__ double pcfm_elem(double a, double b, double x, double z, double tau,
+                                            double rest, double sigma0, int first) {
+  const double ut = first ? a : a + tau * (b - a);
+  return ut + rest * ((x - a) + sigma0 * rest * z);
+}
+
+// u_hat_1 for step tau over n values (pairs, then the odd last value); first = (tau == 0):
+// u_tau = u_0 and u_1 is not read.
 __global__ void __launch_bounds__(256)
-k_pcfm_step(long long n2, double tau, double sigma0, int first,
+k_pcfm_step(long long n, double tau, double sigma0, int first,
             const double2 *__restrict__ u0, const double2 *__restrict__ u1,
             const double2 *__restrict__ x1, const double2 *__restrict__ xi,
             double2 *__restrict__ uh) {
   const double rest = 1.0 - tau;
+  const long long n2 = n >> 1;
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const long long j = n - 1;
+    const double *a = (const double *)u0, *b = (const double *)u1;
+    const double *x = (const double *)x1, *z = (const double *)xi;
+    ((double *)uh)[j] = pcfm_elem(a[j], first ? 0.0 : b[j], x[j], z[j], tau, rest, sigma0, first);
+  }
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n2;
        i += (long long)gridDim.x * blockDim.x) {
     const double2 a = __ldg(u0 + i), x = __ldg(x1 + i), z = __ldg(xi + i);
@@ -103,13 +117,14 @@ SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, doub
   so.max_corrections = o.max_corrections;
   so.pad = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  const long long n2 = (long long)B * p->info.n_vars / 2;
-  long long blocks = (n2 + 255) / 256;
+  const long long n = (long long)B * p->info.n_vars;
+  long long blocks = (n / 2 + 255) / 256;
+  if (blocks < 1) blocks = 1;
   if (blocks > 148LL * 8) blocks = 148LL * 8;
   int launches = 0;
   for (int k = 0; k < n_steps; ++k) {
     const double tau = (double)k / (double)n_steps;
-    k_pcfm_step<<<(int)blocks, 256, 0, s>>>(n2, tau, sigma0, k == 0, (const double2 *)u0,
+    k_pcfm_step<<<(int)blocks, 256, 0, s>>>(n, tau, sigma0, k == 0, (const double2 *)u0,
                                            (const double2 *)u, (const double2 *)x1,
                                            (const double2 *)xi, (double2 *)uh);
     launches++;

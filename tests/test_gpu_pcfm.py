@@ -100,3 +100,22 @@ def test_pcfm_errors():
         p.pcfm_sample(*d, n_steps=0)
     with pytest.raises(_abi.SnapError):
         p.pcfm_sample(*d, n_steps=2, sigma0=float("nan"))
+
+
+def test_pcfm_family_d_against_oracle_loop():
+    """The sampling pass on the Burgers boundary-condition rows (family D, odd nx)."""
+    nx, nt, B, N, s0 = 21, 5, 3, 4, 0.2
+    x1, pr = synthetic.gen_burgers_bc(58, B, nx, nt)
+    x1 = x1.reshape(B, -1)
+    rng = np.random.default_rng(59)
+    u0 = rng.normal(size=x1.shape)
+    xi = rng.normal(size=x1.shape)
+    p = Problem("D", nx, nt)
+    u, lam, st, _ = _run(p, u0, x1, xi, pr, N, s0)
+    assert (st["status"] == 0).all()
+    S = problems.structure_bc(nx, nt)
+    b = problems.rhs_bc(nx, nt, pr)
+    ue, le, so = pcfm.sample(lambda y: solve.project(S, b, y), u0, x1, xi, N, s0)
+    assert (so["status"] == 0).all()
+    H.assert_u_close(u, ue)
+    H.assert_lam_close(S, lam, le)
