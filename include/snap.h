@@ -92,7 +92,8 @@ typedef enum {
    * Dirichlet row u_{k,0} = u_L, the mass row dx sum_i u_{k,i} = m0 and the Neumann row
    * u_{k,nx-1} = u_{k,nx-2}.  params[b] = {u_L, m0}; rows grouped by type (nt Dirichlet, nt
    * mass, nt Neumann); nx in [4, 65536] (any parity), desc.rows must be 0.  Linear rows:
-   * one Newton step; snap_project_backward returns SNAP_ERR_UNSUPPORTED for it. */
+   * one Newton step; the adjoint applies the same projector to dL/du (grad_params =
+   * dL/d(u_L, m0)). */
   SNAP_FAMILY_D_BURGERS_BC = 4
 } snap_family;
 

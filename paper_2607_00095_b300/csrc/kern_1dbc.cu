@@ -127,6 +127,74 @@ k1dbc_forward(int B, int nt, int nx, double dx, double inv_det, const double *__
   }
 }
 
+// Adjoint (implicit-function theorem on the linear KKT system; Appendix B's K at the solution
+// does not depend on u for linear rows): K [a; b] = [gbar; 0] gives
+// b = (A A^T)^-1 A gbar and a = dL/du_hat = gbar - A^T b, the same projector as the forward
+// step applied to gbar with zero right-hand side.  dL/du_L = sum_k b_D,k and
+// dL/dm0 = sum_k b_M,k (each right-hand side enters h with a minus sign).  The per-slice
+// (b_D, b_M) go to the workspace; a sample whose forward status is not OK gets NaN.
+__global__ void __launch_bounds__(256)
+k1dbc_backward(int B, int nt, int nx, double dx, double inv_det, const double *__restrict__ gu,
+               const snap_stats *__restrict__ fst, double *__restrict__ gh,
+               double2 *__restrict__ bsum) {
+  const int lane = threadIdx.x & 31;
+  const int q = lane >> 2, r = lane & 3;
+  const long long s = ((((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 3) + q;
+  const bool live = s < (long long)B * nt;
+  const int b = live ? (int)(s / nt) : 0;
+  const double *row = gu + (size_t)(live ? s : 0) * nx;
+  double *out = gh + (size_t)(live ? s : 0) * nx;
+  double p0 = 0.0;
+  if (live)
+    for (int i = r; i < nx; i += 4) p0 += row[i];
+  double S = p0;
+  S += __shfl_xor_sync(FULL, S, 1);
+  S += __shfl_xor_sync(FULL, S, 2);
+  double lD = 0.0, lM = 0.0, lN = 0.0;
+  const bool bad = live && fst && fst[b].status != SNAP_SAMPLE_OK;
+  if (live && r == 0) {
+    const double rd = row[0], rm = dx * S, rn = row[nx - 1] - row[nx - 2];
+    lD = ((double)nx * dx * dx * rd - dx * rm) * inv_det;
+    lM = (rm - dx * rd) * inv_det;
+    lN = 0.5 * rn;
+  }
+  const int src = lane & ~3;
+  lD = __shfl_sync(FULL, lD, src);
+  lM = __shfl_sync(FULL, lM, src);
+  lN = __shfl_sync(FULL, lN, src);
+  if (!live) return;
+  const double c = dx * lM;
+  if (bad) {
+    for (int i = r; i < nx; i += 4) out[i] = NAN;
+  } else {
+    for (int i = r; i < nx; i += 4) out[i] = row[i] - c;
+    if (r == 0) out[0] = (row[0] - c) - lD;
+    if (r == (nx - 2) % 4) out[nx - 2] = (row[nx - 2] - c) + lN;
+    if (r == (nx - 1) % 4) out[nx - 1] = (row[nx - 1] - c) - lN;
+  }
+  if (r == 0) bsum[s] = bad ? make_double2(NAN, NAN) : make_double2(lD, lM);
+}
+
+// dL/d(u_L, m0) per sample: fixed-order sums of the slices' (b_D, b_M).
+__global__ void k1dbc_backward_params(int B, int nt, const double2 *__restrict__ bsum,
+                                      double *__restrict__ gp) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (warp >= B) return;
+  double d = 0.0, m = 0.0;
+  for (int k = lane; k < nt; k += 32) {
+    const double2 v = bsum[(size_t)warp * nt + k];
+    d += v.x;
+    m += v.y;
+  }
+  d = bc_warp_sum(d);
+  m = bc_warp_sum(m);
+  if (lane == 0) {
+    gp[2 * (size_t)warp] = d;
+    gp[2 * (size_t)warp + 1] = m;
+  }
+}
+
 __global__ void __launch_bounds__(256)
 k1dbc_residual(int B, int nt, int nx, double dx, const double *__restrict__ u,
                const double *__restrict__ params, double *__restrict__ h,
@@ -183,6 +251,27 @@ cudaError_t launch_1dbc_forward(const snap_problem *p, int B, const double *u_ha
   int launches = 1;
   if (stats) {
     launch_finalize_stats(B, nt, bst, o.tol_h, stats, s);
+    launches++;
+  }
+  snap_note_launch(launches);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_1dbc_backward(const snap_problem *p, int B, const double *grad_u,
+                                 const snap_stats *stats, double *grad_u_hat, double *grad_params,
+                                 void *ws, cudaStream_t s) {
+  const int nx = p->desc.nx, nt = p->desc.nt;
+  // (b_D, b_M) per slice in the statistics area of the workspace (16 of its 40 bytes / slice)
+  double2 *bsum = (double2 *)ws;
+  const double dx = 1.0 / (nx - 1);
+  const double inv_det = 1.0 / ((double)(nx - 1) * dx * dx);
+  const int pid = snap_prof_begin(s, "k1dbc_backward");
+  k1dbc_backward<<<blocks_for_warps(((long long)B * nt + 7) / 8), 256, 0, s>>>(
+      B, nt, nx, dx, inv_det, grad_u, stats, grad_u_hat, bsum);
+  snap_prof_end(s, pid);
+  int launches = 1;
+  if (grad_params) {
+    k1dbc_backward_params<<<blocks_for_warps(B), 256, 0, s>>>(B, nt, bsum, grad_params);
     launches++;
   }
   snap_note_launch(launches);

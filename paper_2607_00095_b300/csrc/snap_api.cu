@@ -428,8 +428,6 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
   if (st != SNAP_OK) return st;
   if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN)
     return fail(SNAP_ERR_UNSUPPORTED, "the toy family supports pattern queries only");
-  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
-    return fail(SNAP_ERR_UNSUPPORTED, "no adjoint for family D in this build");
   if (B == 0) return SNAP_OK;
   if (!grad_u || !u || !lambda || !params || !grad_u_hat)
     return fail(SNAP_ERR_INVALID_ARG, "null grad_u / u / lambda / params / grad_u_hat");
@@ -439,7 +437,10 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
   if (!workspace || workspace_bytes < need)
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
+  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
+    e = launch_1dbc_backward(p, B, grad_u, stats, grad_u_hat, grad_params, workspace,
+                             (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_backward(p, B, grad_u, u, lambda, params, stats, adjoint_cache, grad_u_hat,
                            grad_params, workspace, (cudaStream_t)stream);
   else

@@ -147,6 +147,9 @@ cudaError_t launch_1dbc_forward(const snap_problem *p, int B, const double *u_ha
                                 const double *params, double *u, double *lambda,
                                 snap_stats *stats, const SolverOpts &o, void *ws,
                                 cudaStream_t s);
+cudaError_t launch_1dbc_backward(const snap_problem *p, int B, const double *grad_u,
+                                 const snap_stats *stats, double *grad_u_hat, double *grad_params,
+                                 void *ws, cudaStream_t s);
 cudaError_t launch_1dbc_residual(const snap_problem *p, int B, const double *u,
                                  const double *params, double *h, double *h_inf, void *ws,
                                  cudaStream_t s);

@@ -65,8 +65,39 @@ def test_bc_edge_cases():
     assert st["status"][1] == 0 and st["iters"][1] == 0
     np.testing.assert_array_equal(u[1], uh[1].ravel())
     assert st["status"][2] == 3
-    with pytest.raises(_abi.SnapError) as ei:
-        p.backward(d["u"], d["u"], d["lam"], d["pr"])
-    assert ei.value.code == 2
     with pytest.raises(_abi.SnapError):
         Problem("D", 3, 4)
+
+
+def test_bc_adjoint_against_oracle_and_fd():
+    nx, nt, B = 13, 4, 3
+    uh, pr = synthetic.gen_burgers_bc(87, B, nx, nt)
+    gbar = synthetic.gen_gbar(88, (B, nx * nt))
+    p = Problem("D", nx, nt)
+    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    gh, gp = p.backward(H.to_dev(gbar), d["u"], d["lam"], d["pr"], stats=d["st"])
+    torch.cuda.synchronize()
+    gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
+    S = problems.structure_bc(nx, nt)
+    a, bl = solve.adjoint(S, u, lam, gbar)
+    np.testing.assert_allclose(gh, a, rtol=0, atol=1e-12 * np.abs(a).max())
+    gpe = np.stack([bl[:, :nt].sum(axis=1), bl[:, nt:2 * nt].sum(axis=1)], axis=1)
+    np.testing.assert_allclose(gp, gpe, rtol=1e-10, atol=1e-12)
+    # central differences of L = gbar . u(u_hat, params)
+    h = 1e-6
+
+    def loss(prm, x):
+        uu, _, _, _, _ = H.run_gpu(p, x, prm)
+        return (uu * gbar).sum(axis=1)
+
+    for j in range(2):
+        pp, pm = pr.copy(), pr.copy()
+        pp[:, j] += h
+        pm[:, j] -= h
+        np.testing.assert_allclose((loss(pp, uh) - loss(pm, uh)) / (2 * h), gp[:, j], rtol=1e-6,
+                                   atol=1e-8)
+    rng = np.random.default_rng(9)
+    for _ in range(4):
+        dr = rng.normal(size=uh.shape)
+        fd = (loss(pr, uh + h * dr) - loss(pr, uh - h * dr)) / (2 * h)
+        np.testing.assert_allclose(fd, (gh * dr.reshape(B, -1)).sum(axis=1), rtol=1e-6, atol=1e-8)
