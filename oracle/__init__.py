@@ -13,6 +13,10 @@ Contents
                   definitions (Table I, Appendix A, Appendix C, Appendix D) and the
                   workload definitions; dh/dtheta for the adjoint.
   solve.py        ctypes wrapper: project(), adjoint(), components().
+  flux.py         family E (Burgers IC + mass + Godunov flux rows, Appendix A and D): the
+                  KKT point by its definition (forward Godunov steps, stationarity solve),
+                  the Newton-KKT iteration on the full system for small cases, the adjoint.
+  pcfm.py         the sampling loop of Eqs. 1-3 around the oracle projection.
   closed_form.py  exact projections with a plain definition (2-D Leray projection onto
                   divergence-free fields intersected with the energy sphere, via FFT).
 

@@ -155,6 +155,21 @@ def gen_burgers_bc(seed, B, nx, nt, noise=0.1, eps=0.02):
     return np.ascontiguousarray(u_hat), np.ascontiguousarray(params)
 
 
+def gen_burgers_flux(seed, B, nx, nt, noise=0.1, eps=0.02):
+    """IC regime of the Burgers problem on [0, 1] (x_i = i / (nx - 1), t_k = k / (nt - 1)):
+    per sample the front u_IC(x) = 1 / (1 + exp((x - p_loc) / eps)), p_loc ~ U(0.2, 0.8),
+    as the IC parameters g = u_IC(x_i), and u_hat = u_IC(x - t / 2) + N(0, noise^2) (the
+    front at the Burgers shock speed 1/2).  Returns (u_hat [B, nt, nx], params [B, nx])."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) / (nx - 1)
+    t = np.arange(nt) / (nt - 1)
+    p_loc = rng.uniform(0.2, 0.8, size=B)
+    xx = x[None, None, :] - 0.5 * t[None, :, None] - p_loc[:, None, None]
+    u_hat = 1.0 / (1.0 + np.exp(np.clip(xx / eps, -700, 700))) + rng.normal(0.0, noise, size=(B, nt, nx))
+    g = 1.0 / (1.0 + np.exp(np.clip((x[None, :] - p_loc[:, None]) / eps, -700, 700)))
+    return np.ascontiguousarray(u_hat), np.ascontiguousarray(g)
+
+
 def gen_pcfm(seed, B, nx, nt, family="B"):
     """Inputs of one PCFM sampling pass on a 1-D family: the data sample x1 and the
     parameters from gen_1d (seed), the prior sample u0 ~ N(0, 1) and the perturbation
@@ -175,4 +190,5 @@ WORKLOADS = {
     "pcfm_1d": dict(family="B", B=512, nx=128, nt=100, seed=1005, n_steps=10, sigma0=0.3),
     "vorticity_2d": dict(B=512, N=16, nt=50, seed=1007),
     "burgers_bc_1d": dict(B=512, nx=101, nt=101, seed=1008),
+    "burgers_flux_1d": dict(B=512, nx=101, nt=101, n_flux=5, seed=1009),
 }
