@@ -232,7 +232,8 @@ def run_ours(args, rank, world, local):
         print(json.dumps({"div_2d": measure_div2d(dev, hbm0), "uneven": measure_uneven(dev),
                           "pcfm": measure_pcfm(dev),
                           "vorticity_2d": measure_vorticity(dev, hbm0),
-                          "burgers_bc_1d": measure_burgers_bc(dev, hbm0)}), flush=True)
+                          "burgers_bc_1d": measure_burgers_bc(dev, hbm0),
+                          "burgers_flux_1d": measure_burgers_flux(dev, hbm0, 5)}), flush=True)
         return 0
     w = WORKLOAD
     B, nx, nt = w["B"], w["nx"], w["nt"]
@@ -439,6 +440,8 @@ def run_ours(args, rank, world, local):
         extra["pcfm"] = measure_pcfm(dev)
         extra["vorticity_2d"] = measure_vorticity(dev, hbm)
         extra["burgers_bc_1d"] = measure_burgers_bc(dev, hbm)
+        extra["burgers_flux_1d"] = measure_burgers_flux(dev, hbm, 5)
+        extra["burgers_flux10_1d"] = measure_burgers_flux(dev, hbm, 10)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -667,6 +670,67 @@ def measure_vorticity(dev, hbm, reps=50):
             "converged_per_call": conv, "projections_per_s": conv / (ms / 1e3),
             "hbm_frac_of_measured_step": bytes_per_call / (ms / 1e3) / 1e9 / hbm,
             "path": "family A rows on flattened frames (nx = N^2), mixed-pipe tile kernel"}
+
+
+def measure_burgers_flux(dev, hbm, K, reps=50):
+    """Family E, the Burgers IC regime with Godunov flux rows: B = 512 samples of
+    nx = nt = 101, IC + mass + Flux(K); four rotating sets (> L2), CUDA graphs."""
+    import torch
+
+    from paper_2607_00095_b300 import Problem, api, decode_stats, synthetic
+    w = synthetic.WORKLOADS["burgers_flux_1d"]
+    B, nx, nt = w["B"], w["nx"], w["nt"]
+    p = Problem("E", nx, nt, n_flux=K)
+    sets = []
+    for r in range(4):
+        uh, g = synthetic.gen_burgers_flux(w["seed"] + 7919 * r, B, nx, nt)
+        d_uh = torch.as_tensor(uh.reshape(B, -1), device=dev)
+        d_pr = torch.as_tensor(g, device=dev)
+        out = (torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        sets.append((d_uh, d_pr, out))
+    ws = p.workspace(B, dev)
+    for d_uh, d_pr, out in sets:
+        p.project(d_uh, d_pr, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    api.profile_reset()
+    api.profile_enable(1)
+    for i in range(12):
+        d_uh, d_pr, out = sets[i % 4]
+        p.project(d_uh, d_pr, out=out, workspace=ws)
+    torch.cuda.synchronize()
+    k_ms, k_n = api.profile_read("k1dflux_forward")
+    api.profile_enable(0)
+    api.profile_reset()
+    cap = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(cap):
+        for d_uh, d_pr, out in sets:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                p.project(d_uh, d_pr, out=out, workspace=ws, stream=cap)
+            graphs.append(g)
+    for g in graphs:
+        g.replay()
+    it = [0]
+
+    def step():
+        graphs[it[0] % 4].replay()
+        it[0] += 1
+    ms = _event_ms(step, reps)
+    conv = 0
+    for d_uh, d_pr, out in sets:
+        _, hinf = p.residual(out[0], d_pr, want_rows=False)
+        st = decode_stats(out[2])
+        conv += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+    conv /= 4
+    bytes_per_call = (8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40) * B
+    kavg = k_ms / max(k_n, 1)
+    return {"workload": f"burgers_flux_1d (Flux({K}))", "B": B, "nx": nx, "nt": nt, "n_flux": K,
+            "ms_per_call": ms, "converged_per_call": conv,
+            "projections_per_s": conv / (ms / 1e3), "kernel": "k1dflux_forward",
+            "kernel_ms": kavg, "hbm_frac_of_measured": bytes_per_call / (kavg / 1e3) / 1e9 / hbm,
+            "algorithmic_bytes_per_call": bytes_per_call}
 
 
 def measure_burgers_bc(dev, hbm, reps=50):

@@ -94,7 +94,20 @@ typedef enum {
    * mass, nt Neumann); nx in [4, 65536] (any parity), desc.rows must be 0.  Linear rows:
    * one Newton step; the adjoint applies the same projector to dL/du (grad_params =
    * dL/d(u_L, m0)). */
-  SNAP_FAMILY_D_BURGERS_BC = 4
+  SNAP_FAMILY_D_BURGERS_BC = 4,
+  /* IC regime of the Burgers problem with Godunov flux rows (Appendix A "IC, mass,
+   * Flux(k)"; the flux residual of Appendix D): 1-D field on x_i = i dx, dx = 1 / (nx - 1),
+   * periodic neighbours, t_k = k dt, dt = 1 / (nt - 1), c = dt / dx.  Rows, in this order:
+   * IC u^0_i = g_i (nx); mass dx sum_i u^k_i = M, M = dx sum_i g_i (nt); flux
+   * u^k_i = G(u^{k-1})_i for k = 1..K, K = desc.n_flux (K nx rows, slice-major), with
+   * G(v)_i = v_i - c (F(v_i, v_{i+1}) - F(v_{i-1}, v_i)) and F the Godunov flux of u^2/2
+   * (minimum of u^2/2 over [a, b] when a <= b, maximum over [b, a] when a > b).  The mass
+   * rows of slices 0..K are implied by the others (lambda 0; counted in h_inf).
+   * params[b] = g[0..nx-1]; nx in [3, 512], 1 <= n_flux <= nt - 1, desc.rows must be 0.
+   * The KKT point is evaluated directly (forward Godunov steps, backward substitution for
+   * the multipliers; stats.iters = 1).  Adjoint: dL/du_hat is 0 on slices 0..K and
+   * gbar - mean(gbar) on the others; grad_params = dL/dg.  u0 must be NULL. */
+  SNAP_FAMILY_E_BURGERS_FLUX = 5
 } snap_family;
 
 /* Row-type bits for snap_problem_desc.rows (1-D families). */
@@ -137,6 +150,7 @@ typedef struct {
   unsigned rows;       /* 1-D: SNAP_ROW_* mask (IC required); 0 = family default */
   double energy_floor; /* 1-D: floor in E_k (the workloads use 0.05) */
   int max_batch;       /* 0, or an upper bound on B checked by every call */
+  int n_flux;          /* family E: Godunov flux steps K (1..nt-1); other families: 0 */
 } snap_problem_desc;
 
 typedef struct {

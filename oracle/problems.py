@@ -41,7 +41,8 @@ ROW_IC, ROW_MASS, ROW_ENERGY, ROW_BOUNDARY, ROW_DIV, ROW_KE, ROW_TOYMASS = range
 ROW_DIRICHLET, ROW_NEUMANN = 7, 8
 ROW_TYPE_NAMES = {ROW_IC: "ic", ROW_MASS: "mass", ROW_ENERGY: "energy",
                   ROW_BOUNDARY: "boundary", ROW_DIV: "div", ROW_KE: "kinetic_energy",
-                  ROW_TOYMASS: "mass", ROW_DIRICHLET: "dirichlet", ROW_NEUMANN: "neumann"}
+                  ROW_TOYMASS: "mass", ROW_DIRICHLET: "dirichlet", ROW_NEUMANN: "neumann",
+                  9: "flux"}
 
 
 @dataclass

@@ -9,7 +9,7 @@ SNAP_OK = 0
 NOALLOC_SCRATCH_BYTES = 8388608
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NO_MEMORY",
                 5: "WORKSPACE", 6: "NOT_READY"}
-FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY, FAMILY_D = 0, 1, 2, 3, 4
+FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY, FAMILY_D, FAMILY_E = 0, 1, 2, 3, 4, 5
 ROW_IC, ROW_MASS, ROW_ENERGY, ROW_BOUNDARY = 1, 2, 4, 8
 PATH_AUTO, PATH_GENERAL, PATH_MOMENT, PATH_MIXED = 0, 1, 2, 3
 SAMPLE_STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH", 3: "NONFINITE", 4: "INFEASIBLE_PARAMS",
@@ -18,7 +18,8 @@ SAMPLE_STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH", 3: "NONFINITE", 4: "INF
 
 class ProblemDesc(C.Structure):
     _fields_ = [("family", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nt", C.c_int),
-                ("rows", C.c_uint), ("energy_floor", C.c_double), ("max_batch", C.c_int)]
+                ("rows", C.c_uint), ("energy_floor", C.c_double), ("max_batch", C.c_int),
+                ("n_flux", C.c_int)]
 
 
 class Info(C.Structure):
@@ -44,6 +45,7 @@ class Schedule(C.Structure):
 
 
 assert C.sizeof(Stats) == 40
+assert C.sizeof(ProblemDesc) == 40
 
 _lib = None
 

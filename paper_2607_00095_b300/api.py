@@ -16,7 +16,7 @@ STATS_DTYPE = np.dtype([("iters", "<i4"), ("backtracks", "<i4"), ("status", "<i4
                         ("corrections", "<i4"), ("h_inf", "<f8"), ("kkt_inf", "<f8"),
                         ("obj", "<f8")])
 FAMILIES = {"A": _abi.FAMILY_A, "B": _abi.FAMILY_B, "C": _abi.FAMILY_C, "toy": _abi.FAMILY_TOY,
-            "D": _abi.FAMILY_D}
+            "D": _abi.FAMILY_D, "E": _abi.FAMILY_E}
 PATHS = {"auto": _abi.PATH_AUTO, "general": _abi.PATH_GENERAL, "moment": _abi.PATH_MOMENT,
          "mixed": _abi.PATH_MIXED}
 
@@ -49,16 +49,17 @@ def decode_stats(st):
 class Problem:
     """One constraint family on one grid (snap_problem_create)."""
 
-    def __init__(self, family, nx, nt, ny=None, rows=0, energy_floor=0.05, max_batch=0):
+    def __init__(self, family, nx, nt, ny=None, rows=0, energy_floor=0.05, max_batch=0, n_flux=0):
         L = lib()
         fam = FAMILIES[family] if isinstance(family, str) else int(family)
         d = _abi.ProblemDesc(fam, nx, ny if ny is not None else (nx if fam == _abi.FAMILY_C else 0),
-                             nt, rows, energy_floor, max_batch)
+                             nt, rows, energy_floor, max_batch, n_flux)
         h = C.c_void_p()
         check(L.snap_problem_create(C.byref(d), C.byref(h)))
         self._h = h
         self.family = family
         self.nx, self.nt = nx, nt
+        self.n_flux = n_flux
         info = _abi.Info()
         check(L.snap_problem_info(h, C.byref(info)))
         self.n_vars = info.n_vars

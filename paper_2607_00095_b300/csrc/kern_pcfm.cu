@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "kern_1dflux.h"
 #include "snap_internal.h"
 
 namespace {
@@ -58,8 +59,9 @@ bool aligned16p(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 size_t pcfm_ws_bytes(const snap_problem *p, int B) {
   const size_t proj = (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)   ? ws_bytes_2d(p, B)
-                      : (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) ? ws_bytes_1dbc(p, B)
-                                                                     : ws_bytes_1d(p, B);
+                      : (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)   ? ws_bytes_1dbc(p, B)
+                      : (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) ? ws_bytes_1dflux(p, B)
+                                                                       : ws_bytes_1d(p, B);
   return snap_align256(sizeof(double) * (size_t)B * p->info.n_vars) + proj;
 }
 
@@ -135,6 +137,8 @@ SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, doub
                               SNAP_PATH_MIXED, pws, s);
       else if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
         e = launch_1dbc_forward(p, B, uh, params, u, lambda, stats, so, pws, s);
+      else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
+        e = launch_1dflux_forward(p, B, uh, params, u, lambda, stats, so, pws, s);
       else
         e = launch_1d_forward(p, B, uh, params, nullptr, u, lambda, stats, nullptr, so,
                               SNAP_PATH_MIXED, pws, s);

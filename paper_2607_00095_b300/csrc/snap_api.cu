@@ -8,6 +8,7 @@
 
 #include <vector>
 
+#include "kern_1dflux.h"
 #include "snap_internal.h"
 
 namespace {
@@ -131,6 +132,40 @@ void build_pattern_bc(snap_problem *p, int nx, int nt) {
   p->info.n_rows_active = m;
 }
 
+// 1-D family E: IC rows, mass rows (those of slices 0..K implied: inactive), then the flux
+// rows of steps 1..K (u^k_i and u^{k-1}_{i-1,i,i+1}, periodic).
+void build_pattern_flux(snap_problem *p, int nx, int nt, int K) {
+  std::vector<int> rp(1, 0), ci;
+  std::vector<unsigned char> act;
+  for (int i = 0; i < nx; ++i) { ci.push_back(i); rp.push_back((int)ci.size()); act.push_back(1); }
+  for (int k = 0; k < nt; ++k) {
+    for (int i = 0; i < nx; ++i) ci.push_back(k * nx + i);
+    rp.push_back((int)ci.size());
+    act.push_back(k > K ? 1 : 0);
+  }
+  for (int k = 1; k <= K; ++k)
+    for (int i = 0; i < nx; ++i) {
+      const int prev = (k - 1) * nx;
+      ci.push_back(prev + (i + nx - 1) % nx);
+      ci.push_back(prev + i);
+      ci.push_back(prev + (i + 1) % nx);
+      ci.push_back(k * nx + i);
+      rp.push_back((int)ci.size());
+      act.push_back(1);
+    }
+  const int m = (int)rp.size() - 1;
+  p->row_ptr = (int *)malloc(sizeof(int) * rp.size());
+  p->col_idx = (int *)malloc(sizeof(int) * (ci.size() + 1));
+  p->active = (unsigned char *)malloc(m + 1);
+  memcpy(p->row_ptr, rp.data(), sizeof(int) * rp.size());
+  memcpy(p->col_idx, ci.data(), sizeof(int) * ci.size());
+  memcpy(p->active, act.data(), m);
+  int na = 0;
+  for (unsigned char a : act) na += a;
+  p->info.pattern_nnz = (long long)ci.size();
+  p->info.n_rows_active = na;
+}
+
 // 2-D family C: divergence rows [f][j][i] (4 stencil columns), then one energy row per frame.
 void build_pattern_2d(snap_problem *p, int N, int nt) {
   std::vector<int> rp(1, 0), ci;
@@ -179,6 +214,7 @@ snap_status check_batch(const snap_problem *p, int B) {
 size_t ws_bytes(const snap_problem *p, int B) {
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) return ws_bytes_2d(p, B);
   if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) return ws_bytes_1dbc(p, B);
+  if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) return ws_bytes_1dflux(p, B);
   return ws_bytes_1d(p, B);
 }
 
@@ -219,6 +255,8 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
   if (!d || !out) return fail(SNAP_ERR_INVALID_ARG, "null descriptor or output");
   if (d->nt < 2 || d->nt > (1 << 20)) return fail(SNAP_ERR_INVALID_ARG, "nt must be in [2, 2^20]");
   if (d->max_batch < 0) return fail(SNAP_ERR_INVALID_ARG, "max_batch must be >= 0");
+  if (d->family != SNAP_FAMILY_E_BURGERS_FLUX && d->n_flux != 0)
+    return fail(SNAP_ERR_INVALID_ARG, "n_flux is a family E field (must be 0)");
   snap_problem *p = (snap_problem *)calloc(1, sizeof(snap_problem));
   if (!p) return fail(SNAP_ERR_NO_MEMORY, "host allocation failed");
   p->desc = *d;
@@ -304,6 +342,20 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
       build_pattern_bc(p, d->nx, d->nt);
       break;
     }
+    case SNAP_FAMILY_E_BURGERS_FLUX: {
+      if (d->nx < 3 || d->nx > 512 || d->nt < 2 || d->rows != 0 || d->n_flux < 1 ||
+          d->n_flux > d->nt - 1) {
+        free(p);
+        return fail(SNAP_ERR_INVALID_ARG,
+                    "family E: nx in [3, 512], nt >= 2, 1 <= n_flux <= nt - 1, rows 0");
+      }
+      p->info.n_vars = d->nx * d->nt;
+      p->info.n_rows_nominal = d->nx + d->nt + d->n_flux * d->nx;
+      p->info.n_params = d->nx;
+      p->info.n_blocks = d->nt - d->n_flux;
+      build_pattern_flux(p, d->nx, d->nt, d->n_flux);
+      break;
+    }
     case SNAP_FAMILY_TOY_LEFT_RIEMANN: {
       if (d->nx < 2 || d->nx > 4096) {
         free(p);
@@ -366,7 +418,8 @@ snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes) {
   if (st != SNAP_OK) return st;
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) *bytes = cache_bytes_2d(p, B);
   else if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN ||
-           p->desc.family == SNAP_FAMILY_D_BURGERS_BC) *bytes = 0;
+           p->desc.family == SNAP_FAMILY_D_BURGERS_BC ||
+           p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) *bytes = 0;
   else *bytes = sizeof(SliceFactor) * (size_t)B * p->g1.nt;
   return SNAP_OK;
 }
@@ -406,6 +459,10 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
     if (u0) return fail(SNAP_ERR_UNSUPPORTED, "family D starts at u_hat (linear rows: one step)");
     e = launch_1dbc_forward(p, B, u_hat, params, u, lambda, stats, so, workspace,
                             (cudaStream_t)stream);
+  } else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) {
+    if (u0) return fail(SNAP_ERR_UNSUPPORTED, "family E starts at u_hat (direct evaluation)");
+    e = launch_1dflux_forward(p, B, u_hat, params, u, lambda, stats, so, workspace,
+                              (cudaStream_t)stream);
   } else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_forward(p, B, u_hat, params, u0, u, lambda, stats, adjoint_cache, so, path,
                           workspace, (cudaStream_t)stream);
@@ -440,6 +497,9 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
   if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
     e = launch_1dbc_backward(p, B, grad_u, stats, grad_u_hat, grad_params, workspace,
                              (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
+    e = launch_1dflux_backward(p, B, grad_u, u, stats, grad_u_hat, grad_params, workspace,
+                               (cudaStream_t)stream);
   else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_backward(p, B, grad_u, u, lambda, params, stats, adjoint_cache, grad_u_hat,
                            grad_params, workspace, (cudaStream_t)stream);
@@ -468,6 +528,8 @@ snap_status snap_constraint_residual(snap_problem_t p, int B, const double *u,
   cudaError_t e;
   if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
     e = launch_1dbc_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
+    e = launch_1dflux_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
   else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
     e = launch_2d_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
   else

@@ -134,3 +134,32 @@ def test_workspace_and_cache_sizes():
     p = Problem("B", 128, 100)
     assert p.workspace_bytes(512) > p.workspace_bytes(1) > 0
     assert p.cache_bytes(512) == 512 * 100 * 64
+
+
+@pytest.mark.parametrize("nx,nt,K", [(5, 4, 1), (12, 7, 3), (9, 3, 2)])
+def test_pattern_flux_matches_oracle(nx, nt, K):
+    """Family E: the pattern covers every entry of the oracle's Jacobian at a generic point,
+    with one row per nominal row, and the active mask leaves out mass rows 0..K."""
+    from oracle import flux
+    p = Problem("E", nx, nt, n_flux=K)
+    n, m = flux.sizes(nx, nt, K)
+    assert (p.n_vars, p.n_rows, p.n_params) == (n, m, nx)
+    rp, ci = p.pattern()
+    u = np.random.default_rng(5).uniform(-1, 1, size=n)
+    J = flux.full_jacobian(nx, nt, K, u)
+    P = np.zeros((m, n), bool)
+    for r in range(m):
+        P[r, ci[rp[r]:rp[r + 1]]] = True
+    assert not (np.abs(J) > 0)[~P].any()
+    np.testing.assert_array_equal(p.active_rows(), flux.active_rows(nx, nt, K))
+    assert p.n_rows_active == int(flux.active_rows(nx, nt, K).sum())
+
+
+@pytest.mark.parametrize("kw", [dict(nx=2, nt=4, n_flux=1), dict(nx=8, nt=4, n_flux=0),
+                                dict(nx=8, nt=4, n_flux=4), dict(nx=600, nt=4, n_flux=1),
+                                dict(nx=8, nt=4, n_flux=1, rows=1)])
+def test_flux_bad_descriptors_rejected(kw):
+    with pytest.raises(_abi.SnapError):
+        Problem("E", **kw)
+    with pytest.raises(_abi.SnapError):
+        Problem("D", 8, 4, n_flux=1)
