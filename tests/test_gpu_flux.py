@@ -39,21 +39,23 @@ def _check(nx, nt, K, B, seed, g_shift=0.0):
     return p, u, lam, st, d, uh, g
 
 
+# dt/dx <= 1 (the paper's 101 x 101 grid has dt/dx = 1) except for single steps: beyond the
+# CFL limit the Godunov chain grows by up to 2 dt/dx per step and ||h|| grows with it
 @pytest.mark.parametrize("nx,nt,K,B,seed", [
-    (12, 7, 1, 3, 90),        # one flux step
-    (101, 12, 5, 4, 91),      # the paper's Flux(5) on its 101-point grid, fewer slices
-    (101, 101, 10, 3, 92),    # Flux(10) at dt/dx = 1
-    (37, 20, 19, 2, 93),      # K = nt - 1: no mass slices
-    (64, 9, 3, 9, 94),        # B not a multiple of the chain block's four samples
+    (12, 7, 1, 3, 90),        # one flux step, dt/dx = 11/6
+    (41, 41, 5, 4, 91),       # Flux(5), dt/dx = 1
+    (101, 101, 10, 3, 92),    # Flux(10) on the paper's grid
+    (20, 37, 36, 2, 93),      # K = nt - 1: no mass slices
+    (9, 64, 3, 9, 94),        # B not a multiple of the chain block's four samples
     (3, 2, 1, 2, 95),         # smallest grid
-    (512, 8, 2, 2, 96)])      # largest nx
+    (512, 512, 2, 2, 96)])    # largest nx
 def test_flux_against_oracle(nx, nt, K, B, seed):
     _check(nx, nt, K, B, seed)
 
 
 def test_flux_signed_data():
     """Data of both signs (transonic rarefactions, left- and right-moving shocks)."""
-    nx, nt, K, B = 40, 30, 6, 3
+    nx, nt, K, B = 40, 45, 6, 3
     uh, _ = synthetic.gen_burgers_flux(97, B, nx, nt)
     g = np.random.default_rng(98).uniform(-1, 1, size=(B, nx))
     p = Problem("E", nx, nt, n_flux=K)
@@ -81,7 +83,7 @@ def test_flux_full_size_sampled(K):
 
 
 def test_flux_batch_independence_and_nan():
-    nx, nt, K, B = 24, 10, 3, 6
+    nx, nt, K, B = 10, 24, 3, 6
     uh, g = synthetic.gen_burgers_flux(99, B, nx, nt)
     p = Problem("E", nx, nt, n_flux=K)
     u, lam, st, _, _ = H.run_gpu(p, uh, g)
@@ -91,7 +93,7 @@ def test_flux_batch_independence_and_nan():
     np.testing.assert_array_equal(lp, lam[perm])
     uh2 = uh.copy()
     uh2[2, 1, 4] = np.nan          # a chain slice
-    uh2[4, 8, 0] = np.nan          # a mass slice
+    uh2[4, 18, 0] = np.nan         # a mass slice
     u2, _, st2, _, _ = H.run_gpu(p, uh2, g)
     assert st2["status"][2] == 3 and st2["status"][4] == 3
     ok = [0, 1, 3, 5]
@@ -100,7 +102,7 @@ def test_flux_batch_independence_and_nan():
 
 
 def test_flux_adjoint_against_oracle_and_fd():
-    nx, nt, K, B = 16, 9, 3, 3
+    nx, nt, K, B = 9, 16, 3, 3
     uh, g = synthetic.gen_burgers_flux(100, B, nx, nt)
     g = g + 0.05                   # flux arguments away from the switches of F
     gbar = synthetic.gen_gbar(101, (B, nx * nt))
@@ -118,7 +120,7 @@ def test_flux_adjoint_against_oracle_and_fd():
         uu, _, _, _, _ = H.run_gpu(p, x, gg)
         return (uu * gbar).sum(axis=1)
 
-    for i in range(0, nx, 5):
+    for i in range(0, nx, 3):
         dg = np.zeros_like(g)
         dg[:, i] = e
         np.testing.assert_allclose((loss(g + dg, uh) - loss(g - dg, uh)) / (2 * e), gp[:, i],
@@ -131,7 +133,7 @@ def test_flux_adjoint_against_oracle_and_fd():
 
 
 def test_flux_adjoint_nan_for_failed_samples():
-    nx, nt, K, B = 10, 6, 2, 3
+    nx, nt, K, B = 6, 10, 2, 3
     uh, g = synthetic.gen_burgers_flux(102, B, nx, nt)
     uh[1, 4, 3] = np.nan
     gbar = synthetic.gen_gbar(103, (B, nx * nt))
