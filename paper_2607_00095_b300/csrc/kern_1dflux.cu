@@ -16,10 +16,11 @@
 // and every later slice only carries its mass row: u^k = u_hat^k + (sum g - sum u_hat^k)/nx.
 // Generalised Jacobian of F at its switches: the branch chosen by the comparisons below.
 //
-// One launch: the first ceil(B/4) blocks run one warp per sample through the K steps (the
-// time chain is sequential; slices live in shared memory, the multipliers' recursion reads the
-// slices back from u), the other blocks give each mass slice four lanes (eight per warp), as
-// the boundary-condition family does.  stats.iters = 1: one structured solve, no iteration.
+// Two kernels: k1dflux_chain runs one warp per sample through the K steps and back (the time
+// chain is sequential; the slice lives in registers and shared memory, the multipliers'
+// recursion reads the slices back from u), and k1dflux_mass, its programmatic dependent,
+// gives each mass slice four lanes (eight per warp), as the boundary-condition family does,
+// while the chains run.  stats.iters = 1: one structured solve, no iteration.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -88,88 +89,6 @@ __device__ __forceinline__ void put_stat(BlockStat *dst, double hinf, double obj
   *dst = st;
 }
 
-// One sample's time chain (slices 0..K), one warp; sv, sf, sn: 3 nx doubles of shared memory.
-__device__ __forceinline__ void flux_chain(const FluxArgs &a, int b, int lane, double *sv,
-                                           double *sf, double *sn) {
-  const int nx = a.nx, nt = a.nt, K = a.K;
-  const size_t base = (size_t)b * nt * nx;
-  const double *uh = a.uh + base;
-  double *u = a.u + base;
-  double *lam = a.lam + (size_t)b * ((size_t)nx + nt + (size_t)K * nx);
-  const double *g = a.g + (size_t)b * nx;
-  BlockStat *bst = a.bst + (size_t)b * nt;
-  double sg = 0.0, ob = 0.0;
-  for (int i = lane; i < nx; i += 32) {
-    const double v = g[i];
-    sv[i] = v;
-    u[i] = v;
-    sg += v;
-    const double d = v - uh[i];
-    ob = fma(d, d, ob);
-  }
-  sg = fx_warp_sum(sg);
-  ob = fx_warp_sum(ob);
-  const double M = a.dx * sg;
-  if (lane == 0) put_stat(bst, fabs(a.dx * sg - M), 0.5 * ob);
-  for (int k = lane; k <= K; k += 32) lam[nx + k] = 0.0;   // implied mass rows
-  // forward substitution: u^k = G(u^{k-1})
-  for (int k = 1; k <= K; ++k) {
-    __syncwarp();
-    for (int i = lane; i < nx; i += 32) sf[i] = gd_flux(sv[i], sv[i + 1 == nx ? 0 : i + 1]);
-    __syncwarp();
-    const double *uhk = uh + (size_t)k * nx;
-    double *uk = u + (size_t)k * nx;
-    double s = 0.0, o = 0.0;
-    for (int i = lane; i < nx; i += 32) {
-      const double v = gd_update(sv[i], sf[i], sf[i == 0 ? nx - 1 : i - 1], a.c);
-      sn[i] = v;
-      uk[i] = v;
-      s += v;
-      const double d = v - uhk[i];
-      o = fma(d, d, o);
-    }
-    s = fx_warp_sum(s);
-    o = fx_warp_sum(o);
-    if (lane == 0) put_stat(bst + k, fabs(a.dx * s - M), 0.5 * o);
-    double *t = sv;
-    sv = sn;
-    sn = t;
-  }
-  // backward substitution for the multipliers; sv holds u^K
-  __syncwarp();
-  double *w = sn, *sa = sf, *sb = sv;
-  {
-    const double *uhK = uh + (size_t)K * nx;
-    double *lk = lam + nx + nt + (size_t)(K - 1) * nx;
-    for (int i = lane; i < nx; i += 32) {
-      const double v = uhK[i] - sv[i];
-      w[i] = v;
-      lk[i] = v;
-    }
-  }
-  for (int j = K - 1; j >= 0; --j) {
-    __syncwarp();
-    const double *uj = u + (size_t)j * nx;
-    for (int i = lane; i < nx; i += 32) {
-      const int ip = i + 1 == nx ? 0 : i + 1;
-      double da, db;
-      gd_dflux(uj[i], uj[ip], da, db);
-      const double d = w[ip] - w[i];
-      sa[i] = da * d;
-      sb[i] = db * d;
-    }
-    __syncwarp();
-    const double *uhj = uh + (size_t)j * nx;
-    double *lj = j > 0 ? lam + nx + nt + (size_t)(j - 1) * nx : lam;
-    for (int i = lane; i < nx; i += 32) {
-      const double jt = w[i] + a.c * (sa[i] + sb[i == 0 ? nx - 1 : i - 1]);
-      const double v = (uhj[i] - uj[i]) + jt;
-      w[i] = v;
-      lj[i] = v;
-    }
-  }
-}
-
 // Mass slices k = K+1..nt-1: four lanes per slice (eight slices per warp).
 __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int lane) {
   const int q = lane >> 2, r = lane & 3;
@@ -179,21 +98,33 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
   const int b = live ? (int)(s / nm) : 0, k = live ? a.K + 1 + (int)(s % nm) : 0;
   const size_t off = ((size_t)b * a.nt + k) * nx;
   const double *row = a.uh + off;
-  const double *g = a.g + (size_t)b * nx;
-  double S = 0.0, Gs = 0.0;
+  double S = 0.0;
   if (live) {
-    for (int i = r; i < nx; i += 4) {
-      S += row[i];
-      Gs += g[i];
-    }
+#pragma unroll 8
+    for (int i = r; i < nx; i += 4) S += row[i];
   }
   S += __shfl_xor_sync(FULL, S, 1);
   S += __shfl_xor_sync(FULL, S, 2);
-  Gs += __shfl_xor_sync(FULL, Gs, 1);
-  Gs += __shfl_xor_sync(FULL, Gs, 2);
+  // sum g of each distinct sample among the warp's eight slices (usually one or two): a
+  // full-warp sum, the same bits whichever warp computes it
+  double Gs = 0.0, cur = 0.0;
+  int cb = -1;
+  for (int qq = 0; qq < 8; ++qq) {
+    const int bq = __shfl_sync(FULL, b, qq * 4);
+    if (!__shfl_sync(FULL, live ? 1 : 0, qq * 4)) break;   // live slices are a prefix
+    if (bq != cb) {
+      const double *g = a.g + (size_t)bq * nx;
+      double t = 0.0;
+      for (int i = lane; i < nx; i += 32) t += g[i];
+      cur = fx_warp_sum(t);
+      cb = bq;
+    }
+    if (q == qq) Gs = cur;
+  }
   if (!live) return;
   const double sh = (Gs - S) / (double)nx;
   double *out = a.u + off;
+#pragma unroll 8
   for (int i = r; i < nx; i += 4) out[i] = row[i] + sh;
   if (r == 0) {
     a.lam[(size_t)b * ((size_t)nx + a.nt + (size_t)a.K * nx) + nx + k] = -sh / a.dx;
@@ -202,18 +133,153 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k1dflux_forward(FluxArgs a) {
+// The time chain with the sample's slice in registers (lane l holds i = l + 32 m, m < MAXM,
+// nx <= 32 MAXM): each step's global loads are issued one step ahead, so a step costs one
+// round trip instead of one per element.  The same arithmetic as flux_chain (the same bits).
+template <int MAXM>
+__global__ void __launch_bounds__(kThreads) k1dflux_chain(FluxArgs a) {
   extern __shared__ double fx_smem[];
+  // the mass kernel is independent of this one: let it start now
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  if ((int)blockIdx.x < a.n_chain_blocks) {
-    const int b = (int)blockIdx.x * kChainWarps + wib;
-    if (b >= a.B) return;
-    double *sv = fx_smem + (size_t)wib * 3 * a.nx;
-    flux_chain(a, b, lane, sv, sv + a.nx, sv + 2 * a.nx);
-    return;
+  const int b = (int)blockIdx.x * kChainWarps + wib;
+  if (b >= a.B) return;
+  const int nx = a.nx, nt = a.nt, K = a.K;
+  const double c = a.c;
+  double *sv = fx_smem + (size_t)wib * 3 * nx, *sa = sv + nx, *sw = sa + nx;
+  const size_t base = (size_t)b * nt * nx;
+  const double *__restrict__ uh = a.uh + base;
+  double *__restrict__ u = a.u + base;
+  double *__restrict__ lam = a.lam + (size_t)b * ((size_t)nx + nt + (size_t)K * nx);
+  const double *__restrict__ g = a.g + (size_t)b * nx;
+  BlockStat *bst = a.bst + (size_t)b * nt;
+  double v[MAXM], uc[MAXM], un[MAXM];
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    const int i = lane + 32 * m;
+    v[m] = i < nx ? g[i] : 0.0;
+    uc[m] = i < nx ? uh[i] : 0.0;
+    un[m] = i < nx ? uh[nx + i] : 0.0;
   }
-  const long long wid = ((long long)(blockIdx.x - a.n_chain_blocks) * kThreads + threadIdx.x) >> 5;
-  flux_mass(a, wid, lane);
+  double sg = 0.0, ob = 0.0;
+#pragma unroll
+  for (int m = 0; m < MAXM; ++m) {
+    const int i = lane + 32 * m;
+    if (i < nx) {
+      sv[i] = v[m];
+      u[i] = v[m];
+      sg += v[m];
+      const double d = v[m] - uc[m];
+      ob = fma(d, d, ob);
+    }
+  }
+  sg = fx_warp_sum(sg);
+  ob = fx_warp_sum(ob);
+  const double M = a.dx * sg;
+  if (lane == 0) put_stat(bst, fabs(a.dx * sg - M), 0.5 * ob);
+  for (int k = lane; k <= K; k += 32) lam[nx + k] = 0.0;   // implied mass rows
+  // forward substitution: u^k = G(u^{k-1})
+  for (int k = 1; k <= K; ++k) {
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      uc[m] = un[m];
+      un[m] = (k < K && i < nx) ? uh[(size_t)(k + 1) * nx + i] : 0.0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nx) sa[i] = gd_flux(v[m], sv[i + 1 == nx ? 0 : i + 1]);
+    }
+    __syncwarp();
+    double *uk = u + (size_t)k * nx;
+    double sm = 0.0, o = 0.0;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nx) {
+        const double w = gd_update(v[m], sa[i], sa[i == 0 ? nx - 1 : i - 1], c);
+        v[m] = w;
+        sv[i] = w;
+        uk[i] = w;
+        sm += w;
+        const double d = w - uc[m];
+        o = fma(d, d, o);
+      }
+    }
+    sm = fx_warp_sum(sm);
+    o = fx_warp_sum(o);
+    if (lane == 0) put_stat(bst + k, fabs(a.dx * sm - M), 0.5 * o);
+  }
+  // backward substitution: w = lambda^(j+1) in registers (and in sw for the neighbours)
+  double w[MAXM], uj[MAXM];
+  {
+    double *lk = lam + nx + nt + (size_t)(K - 1) * nx;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      w[m] = uc[m] - v[m];
+      if (i < nx) {
+        sw[i] = w[m];
+        lk[i] = w[m];
+      }
+      // slice K-1 (u and u_hat) for the first backward step
+      uj[m] = i < nx ? u[(size_t)(K - 1) * nx + i] : 0.0;
+      un[m] = i < nx ? uh[(size_t)(K - 1) * nx + i] : 0.0;
+    }
+  }
+  for (int j = K - 1; j >= 0; --j) {
+    double ujc[MAXM], pa[MAXM];
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      ujc[m] = uj[m];
+      uc[m] = un[m];
+      uj[m] = (j > 0 && i < nx) ? u[(size_t)(j - 1) * nx + i] : 0.0;
+      un[m] = (j > 0 && i < nx) ? uh[(size_t)(j - 1) * nx + i] : 0.0;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nx) sv[i] = ujc[m];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nx) {
+        const int ip = i + 1 == nx ? 0 : i + 1;
+        double da, db;
+        gd_dflux(ujc[m], sv[ip], da, db);
+        const double d = sw[ip] - w[m];
+        pa[m] = da * d;      // used by this lane only
+        sa[i] = db * d;      // used by the right neighbour
+      }
+    }
+    __syncwarp();
+    double *lj = j > 0 ? lam + nx + nt + (size_t)(j - 1) * nx : lam;
+#pragma unroll
+    for (int m = 0; m < MAXM; ++m) {
+      const int i = lane + 32 * m;
+      if (i < nx) {
+        const double jt = w[m] + c * (pa[m] + sa[i == 0 ? nx - 1 : i - 1]);
+        w[m] = (uc[m] - ujc[m]) + jt;
+        sw[i] = w[m];
+        lj[i] = w[m];
+      }
+    }
+  }
+}
+
+// Mass slices, the programmatic dependent of the chain kernel: it streams while the chains
+// run, and every thread ends by waiting for the chain grid, so that this grid completes after
+// it (the statistics kernel waits for this one).
+__global__ void __launch_bounds__(kThreads) k1dflux_mass(FluxArgs a) {
+  const long long wid = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
+  flux_mass(a, wid, threadIdx.x & 31);
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Adjoint (implicit-function theorem, Appendix B's K at the solution): K [a; b] = [gbar; 0].
@@ -379,7 +445,8 @@ double courant(int nx, int nt) { return (1.0 / (nt - 1)) / (1.0 / (nx - 1)); }
 struct Grid {
   int n_chain_blocks;
   long long n_mass;
-  unsigned blocks;
+  unsigned mass_blocks;
+  unsigned blocks;             // chain blocks + mass blocks (the combined adjoint kernel)
   size_t smem;
 };
 
@@ -388,7 +455,8 @@ Grid flux_grid(const snap_problem *p, int B) {
   const int nt = p->desc.nt, K = p->desc.n_flux;
   G.n_chain_blocks = (B + kChainWarps - 1) / kChainWarps;
   G.n_mass = (long long)B * (nt - K - 1);
-  G.blocks = (unsigned)G.n_chain_blocks + blocks_for_warps((G.n_mass + 7) / 8, kThreads);
+  G.mass_blocks = blocks_for_warps((G.n_mass + 7) / 8, kThreads);
+  G.blocks = (unsigned)G.n_chain_blocks + G.mass_blocks;
   G.smem = sizeof(double) * 3 * (size_t)p->desc.nx * kChainWarps;
   return G;
 }
@@ -421,9 +489,28 @@ cudaError_t launch_1dflux_forward(const snap_problem *p, int B, const double *u_
   a.lam = lambda;
   a.bst = (BlockStat *)ws;
   const int pid = snap_prof_begin(s, "k1dflux_forward");
-  k1dflux_forward<<<G.blocks, kThreads, G.smem, s>>>(a);
-  snap_prof_end(s, pid);
+  if (nx <= 128)
+    k1dflux_chain<4><<<G.n_chain_blocks, kThreads, G.smem, s>>>(a);
+  else if (nx <= 256)
+    k1dflux_chain<8><<<G.n_chain_blocks, kThreads, G.smem, s>>>(a);
+  else
+    k1dflux_chain<16><<<G.n_chain_blocks, kThreads, G.smem, s>>>(a);
   int launches = 1;
+  if (G.n_mass > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G.mass_blocks);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k1dflux_mass, a);
+    launches++;
+  }
+  snap_prof_end(s, pid);
   if (stats) {
     launch_finalize_stats(B, nt, a.bst, o.tol_h, stats, s);
     launches++;

@@ -48,7 +48,9 @@ def _check(nx, nt, K, B, seed, g_shift=0.0):
     (20, 37, 36, 2, 93),      # K = nt - 1: no mass slices
     (9, 64, 3, 9, 94),        # B not a multiple of the chain block's four samples
     (3, 2, 1, 2, 95),         # smallest grid
-    (512, 512, 2, 2, 96)])    # largest nx
+    (512, 512, 2, 2, 96),     # largest nx
+    (128, 160, 40, 2, 97),    # a long chain
+    (300, 400, 9, 2, 98)])    # 8 values per lane of the chain kernel
 def test_flux_against_oracle(nx, nt, K, B, seed):
     _check(nx, nt, K, B, seed)
 
