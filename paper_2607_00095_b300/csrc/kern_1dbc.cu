@@ -53,8 +53,19 @@ k1dbc_forward(int B, int nt, int nx, double dx, double inv_det, const double *__
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2, r = lane & 3;
   const long long s = ((((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 3) + q;
-  const bool live = s < (long long)B * nt;
-  const int b = live ? (int)(s / nt) : 0, k = live ? (int)(s % nt) : 0;
+  const long long nsl = (long long)B * nt;
+  const bool live = s < nsl;
+  int b = 0, k = 0;
+  if (live) {
+    if (nsl < (1LL << 31)) {           // 32-bit division (the 64-bit one is a long sequence)
+      const unsigned su = (unsigned)s;
+      b = (int)(su / (unsigned)nt);
+      k = (int)(su - (unsigned)b * (unsigned)nt);
+    } else {
+      b = (int)(s / nt);
+      k = (int)(s % nt);
+    }
+  }
   const double *row = uh + (size_t)(live ? s : 0) * nx;
   double *out = u + (size_t)(live ? s : 0) * nx;
   // F at (u_hat, 0): the rows (the Lagrangian gradient is zero there)
@@ -140,8 +151,9 @@ k1dbc_backward(int B, int nt, int nx, double dx, double inv_det, const double *_
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2, r = lane & 3;
   const long long s = ((((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) << 3) + q;
-  const bool live = s < (long long)B * nt;
-  const int b = live ? (int)(s / nt) : 0;
+  const long long nsl = (long long)B * nt;
+  const bool live = s < nsl;
+  const int b = !live ? 0 : nsl < (1LL << 31) ? (int)((unsigned)s / (unsigned)nt) : (int)(s / nt);
   const double *row = gu + (size_t)(live ? s : 0) * nx;
   double *out = gh + (size_t)(live ? s : 0) * nx;
   double p0 = 0.0;

@@ -34,21 +34,33 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int kThreads = 128;
 constexpr int kChainWarps = kThreads / 32;   // samples per chain block
 
+// Order key of a double for the branch decisions, taken on the integer pipe (FP64 is the
+// scarce pipe): non-negative bit patterns keep their value, negative ones map to
+// INT64_MIN - bits, so that for non-NaN x, y: x <= y iff key(x) <= key(y) (+0 and -0 both
+// map to 0), key(-x) = -key(x), and x + y >= 0 (rounded) iff key(x) >= -key(y) (rounding
+// never changes the sign of a sum).
+__device__ __forceinline__ long long gd_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (-0x7fffffffffffffffLL - 1) - b;
+}
+
 // Godunov flux of f(u) = u^2/2: the minimum of f over [a, b] (a <= b) or its maximum over
 // [b, a] (a > b).  Rounded products, so that the residual kernel reproduces the same bits.
 __device__ __forceinline__ double gd_flux(double a, double b) {
-  if (a <= b) return a > 0.0 ? __dmul_rn(0.5 * a, a) : (b < 0.0 ? __dmul_rn(0.5 * b, b) : 0.0);
-  return a + b >= 0.0 ? __dmul_rn(0.5 * a, a) : __dmul_rn(0.5 * b, b);
+  const long long ka = gd_key(a), kb = gd_key(b);
+  if (ka <= kb) return ka > 0 ? __dmul_rn(0.5 * a, a) : (kb < 0 ? __dmul_rn(0.5 * b, b) : 0.0);
+  return ka >= -kb ? __dmul_rn(0.5 * a, a) : __dmul_rn(0.5 * b, b);
 }
 
-// dF/da and dF/db of the branch taken
+// dF/da and dF/db of the branch taken (a <= b, a > 0, b < 0, a + b >= 0, as in gd_flux)
 __device__ __forceinline__ void gd_dflux(double a, double b, double &da, double &db) {
+  const long long ka = gd_key(a), kb = gd_key(b);
   bool ia, ib;
-  if (a <= b) {
-    ia = a > 0.0;
-    ib = !ia && b < 0.0;
+  if (ka <= kb) {
+    ia = ka > 0;
+    ib = !ia && kb < 0;
   } else {
-    ia = a + b >= 0.0;
+    ia = ka >= -kb;
     ib = !ia;
   }
   da = ia ? a : 0.0;
@@ -69,6 +81,7 @@ __device__ __forceinline__ double fx_warp_sum(double v) {
 struct FluxArgs {
   int B, nt, nx, K;
   double dx, c;
+  double inv_nx, inv_dx;       // 1/nx and 1/dx, rounded on the host
   int n_chain_blocks;
   long long n_mass;            // B (nt - K - 1) mass slices
   const double *uh, *g;        // u_hat [B][nt][nx], params g [B][nx]
@@ -95,7 +108,17 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
   const long long s = wid * 8 + q;
   const bool live = s < a.n_mass;
   const int nm = a.nt - a.K - 1, nx = a.nx;
-  const int b = live ? (int)(s / nm) : 0, k = live ? a.K + 1 + (int)(s % nm) : 0;
+  int b = 0, k = 0;
+  if (live) {
+    if (a.n_mass < (1LL << 31)) {      // 32-bit division (the 64-bit one is a long sequence)
+      const unsigned su = (unsigned)s;
+      b = (int)(su / (unsigned)nm);
+      k = a.K + 1 + (int)(su - (unsigned)b * (unsigned)nm);
+    } else {
+      b = (int)(s / nm);
+      k = a.K + 1 + (int)(s % nm);
+    }
+  }
   const size_t off = ((size_t)b * a.nt + k) * nx;
   const double *row = a.uh + off;
   double S = 0.0;
@@ -122,12 +145,12 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
     if (q == qq) Gs = cur;
   }
   if (!live) return;
-  const double sh = (Gs - S) / (double)nx;
+  const double sh = (Gs - S) * a.inv_nx;
   double *out = a.u + off;
 #pragma unroll 8
   for (int i = r; i < nx; i += 4) out[i] = row[i] + sh;
   if (r == 0) {
-    a.lam[(size_t)b * ((size_t)nx + a.nt + (size_t)a.K * nx) + nx + k] = -sh / a.dx;
+    a.lam[(size_t)b * ((size_t)nx + a.nt + (size_t)a.K * nx) + nx + k] = -sh * a.inv_dx;
     put_stat(a.bst + (size_t)b * a.nt + k, fabs(a.dx * (S + (double)nx * sh) - a.dx * Gs),
              0.5 * (double)nx * sh * sh);
   }
@@ -481,6 +504,8 @@ cudaError_t launch_1dflux_forward(const snap_problem *p, int B, const double *u_
   a.K = p->desc.n_flux;
   a.dx = 1.0 / (nx - 1);
   a.c = courant(nx, nt);
+  a.inv_nx = 1.0 / nx;
+  a.inv_dx = (double)(nx - 1);
   a.n_chain_blocks = G.n_chain_blocks;
   a.n_mass = G.n_mass;
   a.uh = u_hat;

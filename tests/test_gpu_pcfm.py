@@ -119,3 +119,22 @@ def test_pcfm_family_d_against_oracle_loop():
     assert (so["status"] == 0).all()
     H.assert_u_close(u, ue)
     H.assert_lam_close(S, lam, le)
+
+
+def test_pcfm_family_e_against_oracle_loop():
+    """The sampling pass on the Burgers IC + mass + Godunov flux rows (family E)."""
+    from types import SimpleNamespace
+
+    from oracle import flux
+    nx, nt, K, B, N, s0 = 17, 20, 3, 3, 4, 0.2
+    x1, g = synthetic.gen_burgers_flux(60, B, nx, nt)
+    x1 = x1.reshape(B, -1)
+    rng = np.random.default_rng(61)
+    u0 = rng.normal(size=x1.shape)
+    xi = rng.normal(size=x1.shape)
+    p = Problem("E", nx, nt, n_flux=K)
+    u, lam, st, _ = _run(p, u0, x1, xi, g, N, s0)
+    assert (st["status"] == 0).all() and st["h_inf"].max() <= H.H_TOL
+    ue, le, _ = pcfm.sample(lambda y: flux.project(nx, nt, K, g, y), u0, x1, xi, N, s0)
+    H.assert_u_close(u, ue)
+    H.assert_lam_close(SimpleNamespace(row_type=flux.row_types(nx, nt, K)), lam, le)
