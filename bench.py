@@ -726,11 +726,27 @@ def measure_burgers_flux(dev, hbm, K, reps=50):
     conv /= 4
     bytes_per_call = (8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40) * B
     kavg = k_ms / max(k_n, 1)
+    # the adjoint (dL/du_hat and dL/dg) on the first set, kernel time from the same events
+    gbar = torch.as_tensor(synthetic.gen_gbar(w["seed"] + 1, (B, p.n_vars)), device=dev)
+    d_uh, d_pr, out = sets[0]
+    for _ in range(3):
+        p.backward(gbar, out[0], out[1], d_pr, stats=out[2])
+    torch.cuda.synchronize()
+    api.profile_reset()
+    api.profile_enable(1)
+    for _ in range(12):
+        p.backward(gbar, out[0], out[1], d_pr, stats=out[2])
+    torch.cuda.synchronize()
+    b_ms, b_n = api.profile_read("k1dflux_backward")
+    api.profile_enable(0)
+    api.profile_reset()
+    bavg = b_ms / max(b_n, 1)
     return {"workload": f"burgers_flux_1d (Flux({K}))", "B": B, "nx": nx, "nt": nt, "n_flux": K,
             "ms_per_call": ms, "converged_per_call": conv,
             "projections_per_s": conv / (ms / 1e3), "kernel": "k1dflux_forward",
             "kernel_ms": kavg, "hbm_frac_of_measured": bytes_per_call / (kavg / 1e3) / 1e9 / hbm,
-            "algorithmic_bytes_per_call": bytes_per_call}
+            "algorithmic_bytes_per_call": bytes_per_call, "backward_kernel_ms": bavg,
+            "adjoint_forward_ratio": bavg / kavg}
 
 
 def measure_burgers_bc(dev, hbm, reps=50):
