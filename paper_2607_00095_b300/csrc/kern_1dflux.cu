@@ -297,12 +297,13 @@ __global__ void __launch_bounds__(kThreads) k1dflux_chain(FluxArgs a) {
 }
 
 // Mass slices, the programmatic dependent of the chain kernel: it streams while the chains
-// run, and every thread ends by waiting for the chain grid, so that this grid completes after
-// it (the statistics kernel waits for this one).
+// run.  Block 0 ends by waiting for the chain grid, so that this grid completes after it (the
+// statistics kernel waits for this one); the other blocks exit when done and free their
+// slots for the next wave.
 __global__ void __launch_bounds__(kThreads) k1dflux_mass(FluxArgs a) {
   const long long wid = ((long long)blockIdx.x * kThreads + threadIdx.x) >> 5;
   flux_mass(a, wid, threadIdx.x & 31);
-  asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (blockIdx.x == 0) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Adjoint (implicit-function theorem, Appendix B's K at the solution): K [a; b] = [gbar; 0].
