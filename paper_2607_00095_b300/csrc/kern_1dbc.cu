@@ -69,16 +69,11 @@ k1dbc_forward(int B, int nt, int nx, double dx, double inv_det, const double *__
   const double *row = uh + (size_t)(live ? s : 0) * nx;
   double *out = u + (size_t)(live ? s : 0) * nx;
   // F at (u_hat, 0): the rows (the Lagrangian gradient is zero there)
-  double p0 = 0.0, p1 = 0.0;
+  double S = 0.0;
   if (live) {
-    int i = r;
-    for (; i + 4 < nx; i += 8) {
-      p0 += row[i];
-      p1 += row[i + 4];
-    }
-    if (i < nx) p0 += row[i];
+#pragma unroll 8
+    for (int i = r; i < nx; i += 4) S += row[i];
   }
-  double S = p0 + p1;
   S += __shfl_xor_sync(FULL, S, 1);
   S += __shfl_xor_sync(FULL, S, 2);
   double f0 = 0.0, lD = 0.0, lM = 0.0, lN = 0.0;
@@ -106,6 +101,7 @@ k1dbc_forward(int B, int nt, int nx, double dx, double inv_det, const double *__
   if (take) {
     // one FP64 subtraction per element; the three special points are rewritten by the lanes
     // that own them (same thread: program order)
+#pragma unroll 8
     for (int i = r; i < nx; i += 4) out[i] = row[i] - c;
     if (r == 0) out[0] = (row[0] - c) - lD;
     if (r == (nx - 2) % 4) out[nx - 2] = (row[nx - 2] - c) + lN;
