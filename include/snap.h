@@ -27,11 +27,14 @@
  *   - Errors in arguments are reported by the return code and a thread-local message
  *     (snap_last_error).  Per-sample numerical outcomes (non-convergence, non-finite
  *     input, ...) are NOT call errors: they are written to snap_stats.status.
- *   - Device code never traps and never waits on other blocks.
+ *   - Device code never traps and never spins on other blocks (a programmatic dependent
+ *     launch waits for its primary grid through griddepcontrol.wait, a hardware wait).
  *
  * Layouts (x fastest, the flattening of Appendix C):
  *   1-D families A/B:  u[b][k][i], k < nt time slices, i < nx points, x_i = i/nx periodic,
  *                      t_k = k/(nt-1).
+ *   1-D families D/E:  u[b][k][i] as A/B, but x_i = i/(nx-1) on [0, 1] (both ends on the
+ *                      grid; family E's flux update takes periodic neighbours).
  *   2-D family C:      w[b][f][c][j][i], f < nt frames, c = 0 (u) / 1 (v), j = y, i = x,
  *                      N x N periodic grid, dx = 1/N, t_f = f/(nt-1).
  *   Multipliers lambda[b][r] in the nominal row order (rows implied by other rows are
@@ -39,9 +42,13 @@
  *     A/B: IC rows (nx) | mass rows (nt) | energy rows (nt) | boundary rows (nt, family B)
  *          (only the row types enabled in snap_problem_desc.rows, in this order)
  *     C:   divergence rows [f][j][i] (nt*N*N) | kinetic-energy rows (nt)
+ *     D:   Dirichlet rows (nt) | mass rows (nt) | Neumann rows (nt)
+ *     E:   IC rows (nx) | mass rows (nt; slices 0..K implied) | flux rows [k-1][i] (K*nx)
  *   Parameters params[b][*]:
  *     A/B: g[0..nx-1] (IC values), r (energy decay rate), c[0..nt-1] (family B only)
  *     C:   K0, r2  (kinetic energy K_f = K0 exp(-r2 t_f))
+ *     D:   u_L, m0 (Dirichlet value, mass target)
+ *     E:   g[0..nx-1] (IC values; the mass target is dx sum g)
  */
 #ifndef SNAP_H
 #define SNAP_H
