@@ -155,3 +155,17 @@ def test_flux_rejects_u0():
     p = Problem("E", nx, nt, n_flux=K)
     with pytest.raises(_abi.SnapError):
         H.run_gpu(p, uh, g, u0=uh + 0.1)
+
+
+def test_flux_two_shards_equal_one_batch():
+    """The samples shard across ranks with no exchange: two halves projected apart give the
+    bits of the whole batch (outputs and statistics)."""
+    nx, nt, K, B = 33, 40, 5, 10
+    uh, g = synthetic.gen_burgers_flux(105, B, nx, nt)
+    p = Problem("E", nx, nt, n_flux=K)
+    u, lam, st, _, _ = H.run_gpu(p, uh, g)
+    parts = [H.run_gpu(p, uh[s], g[s]) for s in (slice(0, 3), slice(3, B))]
+    np.testing.assert_array_equal(np.concatenate([q[0] for q in parts]), u)
+    np.testing.assert_array_equal(np.concatenate([q[1] for q in parts]), lam)
+    for key in ("status", "iters", "h_inf", "obj"):
+        np.testing.assert_array_equal(np.concatenate([q[2][key] for q in parts]), st[key])
