@@ -329,7 +329,9 @@ SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, doub
  *     to start at zero (every byte a call reads was written earlier in the same call).  Calls
  *     whose work overlaps on the GPU (other streams, other threads) race on the array: order
  *     them on one stream or synchronise between them.
- * Errors: as snap_project, plus UNSUPPORTED for the 2-D family. */
+ * Errors: as snap_project (INVALID_ARG also when u aliases u_hat, or lambda aliases u or
+ * u_hat: in-place calls are refused), plus UNSUPPORTED for families C, D and E.  Like every
+ * entry point it clears snap_last_error() and snap_last_launch_count() on entry. */
 SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double *u_hat,
                                           const double *params, double *u, double *lambda,
                                           snap_stats *stats, const snap_options *opt,

@@ -120,6 +120,17 @@ class Problem:
                 if t.dtype != torch.float64 or not t.is_contiguous():
                     raise ValueError("snap needs contiguous float64 tensors")
 
+    def _check_sizes(self, B, u_hat=None, params=None, u=None, lam=None, st=None):
+        """Every buffer the library reads or writes must hold exactly the problem's sizes
+        for B samples: a short buffer would be written past its end on the device."""
+        want = (("u_hat", u_hat, B * self.n_vars), ("params", params, B * self.n_params),
+                ("u", u, B * self.n_vars), ("lambda", lam, B * self.n_rows),
+                ("stats", st, 40 * B))
+        for name, t, n in want:
+            if t is not None and t.numel() != n:
+                raise ValueError(f"{name} holds {t.numel()} elements; this problem needs {n} "
+                                 f"for B = {B}")
+
     def project(self, u_hat, params, u0=None, opts=None, cache=False, out=None, stream=None,
                 workspace=None):
         """Returns (u [B, n_vars], lambda [B, n_rows], stats uint8 [B, 40], cache or None)."""
@@ -133,6 +144,8 @@ class Problem:
             st = torch.empty(B, 40, dtype=torch.uint8, device=dev)
         else:
             u, lam, st = out
+            self._check_dev(u, lam)
+        self._check_sizes(B, u_hat, params, u, lam, st)
         cb = None
         if cache:
             cb = torch.empty(max(self.cache_bytes(B), 8), dtype=torch.uint8, device=dev)
@@ -150,8 +163,11 @@ class Problem:
         call).  Calls that overlap on the GPU race on that array."""
         B = u_hat.shape[0]
         self._check_dev(u_hat, params, u, lam)
-        if not st.is_cuda or st.dtype != torch.uint8 or st.numel() != 40 * B:
-            raise ValueError("stats must be a CUDA uint8 tensor of 40 bytes per sample")
+        if not st.is_cuda or st.dtype != torch.uint8 or not st.is_contiguous():
+            raise ValueError("stats must be a contiguous CUDA uint8 tensor of 40 bytes per sample")
+        self._check_sizes(B, u_hat, params, u, lam, st)
+        if u.data_ptr() == u_hat.data_ptr() or lam.data_ptr() in (u.data_ptr(), u_hat.data_ptr()):
+            raise ValueError("outputs may not alias inputs")
         o = opts if opts is not None else options()
         check(lib().snap_project_noalloc(self._h, B, _ptr(u_hat), _ptr(params), _ptr(u),
                                          _ptr(lam), _ptr(st), C.byref(o), _stream(stream)))

@@ -224,6 +224,8 @@ void snap_note_launch(int n) { g_launches += n; }
 
 void snap_reset_launches() { g_launches = 0; }
 
+void snap_clear_error() { g_err[0] = 0; }
+
 snap_status snap_fail_msg(snap_status st, const char *msg) { return fail(st, "%s", msg); }
 
 snap_status snap_check_options(const snap_options &o) { return check_opts(o); }

@@ -92,6 +92,7 @@ struct snap_problem {
 
 // Error-message helpers of snap_api.cu for the other entry-point files.
 snap_status snap_fail_msg(snap_status st, const char *msg);
+void snap_clear_error();
 snap_status snap_check_options(const snap_options &o);
 
 // Kernel-launch bookkeeping (per host thread) and optional event timing (snap_profile.cu).

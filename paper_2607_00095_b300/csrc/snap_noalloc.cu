@@ -35,9 +35,11 @@ SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double 
                                           const double *params, double *u, double *lambda,
                                           snap_stats *stats, const snap_options *opt,
                                           snap_stream_t stream) {
+  snap_clear_error();
+  snap_reset_launches();
   if (!p) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null problem");
   if (p->desc.family != SNAP_FAMILY_A_MASS_ENERGY && p->desc.family != SNAP_FAMILY_B_BURGERS_BOUNDARY)
-    return snap_fail_msg(SNAP_ERR_UNSUPPORTED, "snap_project_noalloc supports the 1-D families only");
+    return snap_fail_msg(SNAP_ERR_UNSUPPORTED, "snap_project_noalloc supports families A and B only");
   if (B < 0 || (p->desc.max_batch > 0 && B > p->desc.max_batch))
     return snap_fail_msg(SNAP_ERR_INVALID_ARG, "batch size out of range");
   if (B == 0) return SNAP_OK;
@@ -45,6 +47,10 @@ SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double 
     return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null u_hat / params / u / lambda");
   if ((((uintptr_t)u_hat) & 15u) || (((uintptr_t)u) & 15u))
     return snap_fail_msg(SNAP_ERR_INVALID_ARG, "u_hat and u must be 16-byte aligned");
+  // the prepare kernel writes the IC slice of u while the tile kernel may still be reading
+  // u_hat (programmatic dependent launch), so an in-place call would be undefined
+  if (u == u_hat || (const double *)lambda == u || (const double *)lambda == u_hat)
+    return snap_fail_msg(SNAP_ERR_INVALID_ARG, "outputs may not alias inputs");
   const size_t need = ws_bytes_1d(p, B);
   if (need > (size_t)SNAP_NOALLOC_SCRATCH_BYTES) {
     char msg[160];
@@ -84,6 +90,8 @@ SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double 
   so.pad = 0;
   const cudaError_t e = launch_1d_forward(p, B, u_hat, params, nullptr, u, lambda, stats, nullptr,
                                           so, o.path, scratch, (cudaStream_t)stream);
+  if (e == cudaErrorNotSupported)
+    return snap_fail_msg(SNAP_ERR_UNSUPPORTED, "unsupported request for this family");
   if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   return SNAP_OK;
 }

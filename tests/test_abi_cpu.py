@@ -163,3 +163,39 @@ def test_flux_bad_descriptors_rejected(kw):
         Problem("E", **kw)
     with pytest.raises(_abi.SnapError):
         Problem("D", 8, 4, n_flux=1)
+
+
+def test_noalloc_rejects_aliased_outputs_without_a_device():
+    """snap_project_noalloc returns INVALID_ARG for in-place calls (u == u_hat, lambda == u)
+    before it touches the device: the addresses below are never dereferenced."""
+    L = _abi.lib()
+    p = Problem("B", 128, 100)
+    o = options()
+    a, b, c = C.c_void_p(0x10000), C.c_void_p(0x20000), C.c_void_p(0x30000)
+    for uh, u, lam in [(a, a, c), (a, b, b), (a, b, a)]:
+        rc = L.snap_project_noalloc(p.handle, 2, uh, c, u, lam, None, C.byref(o), None)
+        assert rc == 1
+        assert "alias" in L.snap_last_error().decode()
+    # families outside A and B are refused with a message that names them
+    e = Problem("E", 9, 5, n_flux=1)
+    rc = L.snap_project_noalloc(e.handle, 2, a, c, b, C.c_void_p(0x40000), None, C.byref(o), None)
+    assert rc == 2 and "families A and B" in L.snap_last_error().decode()
+
+
+def test_binding_rejects_short_buffers_without_launching():
+    """The binding compares every buffer with the problem's sizes before any call: a short
+    tensor would otherwise be written past its end on the device."""
+    import torch
+    p = Problem("B", 16, 6)
+    B = 3
+    uh = torch.zeros(B, p.n_vars, dtype=torch.float64)
+    pr = torch.zeros(B, p.n_params, dtype=torch.float64)
+    lam = torch.zeros(B, p.n_rows, dtype=torch.float64)
+    st = torch.zeros(B, 40, dtype=torch.uint8)
+    p._check_sizes(B, uh, pr, uh, lam, st)
+    for bad in [dict(params=pr[:, :-1]), dict(u=uh[:, :-1]), dict(lam=lam[:2]),
+                dict(st=st[:, :39]), dict(u_hat=uh[:2])]:
+        kw = dict(u_hat=uh, params=pr, u=uh, lam=lam, st=st)
+        kw.update(bad)
+        with pytest.raises(ValueError):
+            p._check_sizes(B, **kw)
