@@ -25,7 +25,7 @@
  * invariant, discrete divergence and kinetic-energy rows all have this form).  Hence
  *     J_rj = A_rj + 2 Q_rj u_j,     W = I + sum_r lam_r * 2 diag(Q_r).
  *
- * Globalisation (the paper is silent; these are the readings written down in the design doc):
+ * Globalisation (the paper is silent; the reading taken here):
  *   Newton-Raphson on F(u, lam) = 0 exactly as Appendix B derives it, from u = u0 (default
  *   u_hat), lam = 0; stop when ||F||_inf <= tol_kkt; merit phi = 1/2 ||F||_2^2, for which
  *   the Newton step is a descent direction whenever K is nonsingular; Armijo backtracking

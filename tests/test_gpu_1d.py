@@ -47,9 +47,11 @@ def test_burgers_family_parity_ragged(path, B, nx, nt, seed):
     p = Problem("B", nx, nt)
     u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
     ue, le, so, S, b = _oracle("B", nx, nt, pr, uh)
+    # every sample: the same outcome on both sides (a GPU that converges where the oracle
+    # stalls, or the reverse, fails here), then the values of the converged ones
+    np.testing.assert_array_equal(st["status"], so["status"])
     ok = so["status"] == 0
-    assert ok.any()
-    np.testing.assert_array_equal(st["status"][ok], 0)
+    assert ok.all()
     H.assert_u_close(u[ok], ue[ok])
     H.assert_lam_close(S, lam[ok], le[ok])
     assert st["h_inf"][ok].max() <= H.H_TOL

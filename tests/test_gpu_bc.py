@@ -78,8 +78,11 @@ def test_bc_adjoint_against_oracle_and_fd():
     gh, gp = p.backward(H.to_dev(gbar), d["u"], d["lam"], d["pr"], stats=d["st"])
     torch.cuda.synchronize()
     gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
+    # the oracle's dense adjoint at the oracle's own solution of the same inputs
     S = problems.structure_bc(nx, nt)
-    a, bl = solve.adjoint(S, u, lam, gbar)
+    ue, le, so = solve.project(S, problems.rhs_bc(nx, nt, pr), uh.reshape(B, -1))
+    assert (so["status"] == 0).all()
+    a, bl = solve.adjoint(S, ue, le, gbar)
     np.testing.assert_allclose(gh, a, rtol=0, atol=1e-12 * np.abs(a).max())
     gpe = np.stack([bl[:, :nt].sum(axis=1), bl[:, nt:2 * nt].sum(axis=1)], axis=1)
     np.testing.assert_allclose(gp, gpe, rtol=1e-10, atol=1e-12)

@@ -379,3 +379,38 @@ def test_adjoint_family_a_against_closed_form_fd():
     d = rng.normal(size=uh.shape)
     fd = (loss(pr, uh + h * d) - loss(pr, uh - h * d)) / (2 * h)
     assert abs(fd - np.sum(a * d.reshape(a.shape))) <= 1e-5 * max(1.0, abs(fd))
+
+
+@pytest.mark.parametrize("N", [8, 16])
+def test_adjoint_2d_grad_params_against_closed_form_fd(N):
+    """dL/d(K0, r2) of the 2-D family: the oracle's dense adjoint at its own solution, mapped
+    through grad_params_2d, against central differences of the FFT closed form (a different
+    route to the same projection); also dL/dw_hat along random directions.  A slip in either
+    derivative of K0 exp(-r2 t) (sign, the factor t, the factor K0) fails here."""
+    nt, B = 3, 2
+    wh, pr = synthetic.gen_2d(170 + N, B, N, nt, kmax=min(8, N // 2 - 1))
+    pr = pr.copy()
+    pr[:, 1] = [0.2, 0.7]                     # distinct decay rates per sample
+    gbar = synthetic.gen_gbar(180 + N, (B, nt * 2 * N * N))
+    S = problems.structure_2d(N, nt)
+    u, lam, st = solve.project(S, problems.rhs_2d(N, nt, pr), wh.reshape(B, -1), tol_kkt=1e-13)
+    assert (st["status"] == 0).all()
+    a, bl = solve.adjoint(S, u, lam, gbar)
+    gp = problems.grad_params_2d(N, nt, pr, bl)
+
+    def loss(p, x):
+        w, _ = closed_form.project_2d(x, p)
+        return (w.reshape(B, -1) * gbar).sum(axis=1)
+
+    h = 1e-6
+    for j in range(2):
+        pp, pm = pr.copy(), pr.copy()
+        pp[:, j] += h; pm[:, j] -= h
+        fd = (loss(pp, wh) - loss(pm, wh)) / (2 * h)
+        np.testing.assert_allclose(gp[:, j], fd, rtol=1e-6, atol=1e-9)
+        assert np.all(np.abs(gp[:, j]) > 1e-3)          # the check is not vacuous
+    rng = np.random.default_rng(190 + N)
+    for _ in range(3):
+        d = rng.normal(size=wh.shape)
+        fd = (loss(pr, wh + h * d) - loss(pr, wh - h * d)) / (2 * h)
+        np.testing.assert_allclose((a * d.reshape(B, -1)).sum(axis=1), fd, rtol=1e-6, atol=1e-8)
