@@ -70,6 +70,7 @@ typedef struct {
   int max_corrections;
   int split_components;
   double w_keep;
+  int restore;          /* 1: keep grad_u L = 0 along the iteration (reading R25, start u_hat) */
 } ora_opts;
 
 typedef struct {
@@ -420,7 +421,31 @@ static double half_sq(const double *x, int N) {
   return 0.5 * s;
 }
 
-/* Newton-KKT on one component.  u holds u0 on entry and the result on exit. */
+/* The minimiser of L(., lam) for these row forms: grad_u L = u - u_hat + A^T lam
+ * + 2 diag(sum_r lam_r Q_r) u = W(lam) u - u_hat + A^T lam = 0, so u = W^-1 (u_hat - A^T lam)
+ * with the diagonal W(lam) = I + sum_r lam_r 2 diag(Q_r) (positive along the iteration). */
+static void stationary_u(const comp_t *c, const double *uh, const double *lam, double *wd,
+                         double *u) {
+  const int nv = c->nv;
+  for (int j = 0; j < nv; ++j) { wd[j] = 1.0; u[j] = uh[j]; }
+  for (int k = 0; k < c->mr; ++k) {
+    for (int p = c->ap[k]; p < c->ap[k + 1]; ++p) u[c->ac[p]] -= lam[k] * c->av[p];
+    for (int p = c->qp[k]; p < c->qp[k + 1]; ++p) wd[c->qc[p]] += lam[k] * 2.0 * c->qv[p];
+  }
+  for (int j = 0; j < nv; ++j) u[j] /= wd[j];
+}
+
+/* Newton-KKT on one component.  u holds u0 on entry and the result on exit.
+ *
+ * restore = 0 (reading R14): the primal-dual iterate (u, lam) moves along the Newton-KKT
+ * step of Appendix B, (u, lam) + t (du, dlam).
+ * After the stopping test one polishing step is taken (reading R27, below).
+ *
+ * restore = 1 (reading R25, used when the iteration starts at u0 = u_hat): the same Newton-KKT
+ * step and line search, but every trial point is (u(lam_t), lam_t) with lam_t = lam + t dlam
+ * and u(lam) = argmin_u L(u, lam) (stationary_u), so grad_u L = 0 along the whole iteration
+ * and the Newton-KKT step reduces to S dlam = h with S = J W^-1 J^T.  The start u = u_hat,
+ * lam = 0 is such a point. */
 static void newton_component(const comp_t *c, const double *uh, const double *b, double *u,
                              double *lam, const ora_opts *o, ora_stats *st) {
   const int nv = c->nv, N = c->nv + c->mr;
@@ -430,9 +455,12 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
   double *ut = (double *)malloc(sizeof(double) * (size_t)(nv + 1));
   double *lt = (double *)malloc(sizeof(double) * (size_t)(c->mr + 1));
   double *K = (double *)malloc(sizeof(double) * (size_t)N * N + 8);
+  double *wd = (double *)malloc(sizeof(double) * (size_t)(nv + 1));
+  const int restore = o->restore;
   ldl_t f;
   ldl_alloc(&f, N);
   for (int k = 0; k < c->mr; ++k) lam[k] = 0.0;
+  if (restore) stationary_u(c, uh, lam, wd, u);
   st->iters = 0; st->backtracks = 0; st->status = ORA_OK; st->corrections = 0;
   eval_F(c, u, uh, lam, b, F);
   double phi = half_sq(F, N);
@@ -481,8 +509,11 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
     int nb = 0, accepted = 0;
     double phit = phi;
     for (;;) {
-      for (int j = 0; j < nv; ++j) ut[j] = u[j] + t * dz[j];
       for (int k = 0; k < c->mr; ++k) lt[k] = lam[k] + t * dz[nv + k];
+      if (restore)
+        stationary_u(c, uh, lt, wd, ut);
+      else
+        for (int j = 0; j < nv; ++j) ut[j] = u[j] + t * dz[j];
       eval_F(c, ut, uh, lt, b, Ft);
       phit = half_sq(Ft, N);
       if (phit <= (1.0 - 2.0 * o->c1 * t) * phi) { accepted = 1; break; }
@@ -499,6 +530,37 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
     res = norm_inf(F, N);
     st->iters = it + 1;
   }
+  /* Polishing step (reading R27): the stopping test bounds ||F||, and the multipliers only
+   * through the conditioning of the KKT matrix, which is large on slices whose boundary circle
+   * is nearly degenerate; one more full Newton-KKT step leaves them at the rounding level.  It
+   * is kept when ||F||_inf does not increase (and, with restore, W stays positive); it is not
+   * counted in the iterations. */
+  if (st->status == ORA_OK && c->mr > 0) {
+    build_K(c, u, lam, 0.0, K);
+    double kmax = 0.0;
+    for (int i = 0; i < N * N; ++i) if (fabs(K[i]) > kmax) kmax = fabs(K[i]);
+    ldl_factor(K, &f, (double)N * 2.220446049250313e-16 * (kmax > 0 ? kmax : 1.0));
+    for (int j = 0; j < N; ++j) Ft[j] = -F[j];
+    if (f.n_zero == 0 && ldl_solve(&f, Ft, dz) == 0) {
+      for (int k = 0; k < c->mr; ++k) lt[k] = lam[k] + dz[nv + k];
+      int wpos = 1;
+      if (restore) {
+        stationary_u(c, uh, lt, wd, ut);
+        for (int j = 0; j < nv; ++j) if (!(wd[j] > 0.0)) wpos = 0;
+      } else {
+        for (int j = 0; j < nv; ++j) ut[j] = u[j] + dz[j];
+      }
+      eval_F(c, ut, uh, lt, b, Ft);
+      const double rt = norm_inf(Ft, N);
+      if (wpos && rt <= res) {
+        memcpy(u, ut, sizeof(double) * (size_t)nv);
+        memcpy(lam, lt, sizeof(double) * (size_t)c->mr);
+        memcpy(F, Ft, sizeof(double) * (size_t)N);
+        phi = half_sq(F, N);
+        res = rt;
+      }
+    }
+  }
   /* second-order sufficient condition at a converged point: K has inertia (n, m, 0) iff W
    * is positive definite on null(J) (J of full row rank) */
   if (st->status == ORA_OK && c->mr + nv > 0) {
@@ -511,7 +573,7 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
   st->kkt_inf = res;
   st->phi = phi;
   ldl_free(&f);
-  free(F); free(Ft); free(dz); free(ut); free(lt); free(K);
+  free(F); free(Ft); free(dz); free(ut); free(lt); free(K); free(wd);
 }
 
 /* Adjoint on one component: K [a ; bl] = [gbar ; 0] with K at (u, lam), no correction. */

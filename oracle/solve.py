@@ -16,7 +16,7 @@ ORA_OK, ORA_MAXITER, ORA_LINESEARCH, ORA_NONFINITE, ORA_SINGULAR, ORA_NOT_MINIMU
 class OraOpts(C.Structure):
     _fields_ = [("tol_kkt", C.c_double), ("max_iter", C.c_int), ("max_backtracks", C.c_int),
                 ("c1", C.c_double), ("delta0", C.c_double), ("max_corrections", C.c_int),
-                ("split_components", C.c_int), ("w_keep", C.c_double)]
+                ("split_components", C.c_int), ("w_keep", C.c_double), ("restore", C.c_int)]
 
 
 class OraStats(C.Structure):
@@ -50,7 +50,7 @@ def _p(a, ct):
 
 def default_opts(**kw):
     o = dict(tol_kkt=1e-10, max_iter=50, max_backtracks=30, c1=1e-4, delta0=1e-8,
-             max_corrections=0, split_components=1, w_keep=0.01)
+             max_corrections=0, split_components=1, w_keep=0.01, restore=1)
     o.update(kw)
     return OraOpts(**o)
 
@@ -69,6 +69,9 @@ def project(S, b, u_hat, u0=None, nthreads=0, **opts):
     if u0 is not None:
         u0 = np.ascontiguousarray(np.atleast_2d(u0).reshape(B, -1), np.float64)
         u0p = _p(u0, C.c_double)
+    # R25 (u kept stationary) for the projection's own start u0 = u_hat; an explicit start
+    # point u0 takes the primal-dual iteration of R14
+    opts.setdefault("restore", 0 if u0 is not None else 1)
     o = default_opts(**opts)
     L.ora_project_batch(S.n, S.m, _p(S.a_ptr, C.c_int), _p(S.a_col, C.c_int),
                         _p(S.a_val, C.c_double), _p(S.q_ptr, C.c_int), _p(S.q_col, C.c_int),

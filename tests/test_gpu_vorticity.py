@@ -37,8 +37,11 @@ def test_vorticity_full_size_closed_form_and_conservation():
     H.assert_lam_close(problems.structure_1d("A", N * N, nt), lam, le)
     wv = u.reshape(B, nt, N * N)
     w0 = pr[:, :N * N]
+    # total vorticity per frame is the mass row (dx dy sum = mean here): the stopping test
+    # bounds it by tol_kkt = 1e-10 (the iteration keeps u stationary, so the linear rows
+    # converge with the nonlinear ones rather than in the first full step)
     np.testing.assert_allclose(wv.mean(axis=2), np.repeat(w0.mean(axis=1)[:, None], nt, axis=1),
-                               atol=1e-12)
+                               atol=1e-10)
     np.testing.assert_allclose((wv * wv).mean(axis=2),
                                np.repeat((w0 * w0).mean(axis=1)[:, None], nt, axis=1),
                                rtol=1e-10)

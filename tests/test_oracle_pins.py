@@ -189,10 +189,16 @@ def test_family_a_matches_closed_form_small_1d_workload():
     u, lam, st, S, b = solve.project_1d("A", nx, nt, pr, uh)
     assert (st["status"] == 0).all() and (st["kkt_inf"] <= 1e-10).all()
     np.testing.assert_allclose(u, ue, rtol=0, atol=1e-9)
-    # converged to the rounding floor, u and lambda agree to ~1e-13
+    # converged to the rounding floor, u and lambda agree to ~1e-13 (u = W^-1 (u_hat - A^T lam)
+    # under R25 rounds to within a few hundred ulps of the closed form's arithmetic)
     u, lam, st, S, b = solve.project_1d("A", nx, nt, pr, uh, tol_kkt=1e-13)
     assert (st["status"] == 0).all()
-    np.testing.assert_allclose(u, ue, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(u, ue, rtol=0, atol=3e-13)
+    # the primal-dual iteration of R14 (explicit start u0 = u_hat) reaches the same point
+    u2, lam2, st2, _, _ = solve.project_1d("A", nx, nt, pr, uh, u0=uh, tol_kkt=1e-13)
+    assert (st2["status"] == 0).all()
+    np.testing.assert_allclose(u2, ue, rtol=0, atol=3e-13)
+    np.testing.assert_allclose(lam2, le, rtol=1e-10, atol=1e-11)
     np.testing.assert_allclose(lam, le, rtol=1e-10, atol=1e-11)
     assert st["h_inf"].max() <= 1e-12
 
@@ -237,6 +243,9 @@ def test_family_b_reduces_to_family_a():
     u, lam, st, S, b = solve.project_1d("B", nx, nt, prB, uh)
     assert (st["status"] == 0).all()
     np.testing.assert_allclose(u, ua, atol=1e-12)
+    # multipliers at the rounding floor (at ||F||_inf <= 1e-10 they carry ~ cond * 1e-10)
+    u, lam, st, S, b = solve.project_1d("B", nx, nt, prB, uh, tol_kkt=1e-13)
+    assert (st["status"] == 0).all()
     np.testing.assert_allclose(lam[:, :nx + 2 * nt], la, rtol=1e-9, atol=1e-10)
     np.testing.assert_allclose(lam[:, nx + 2 * nt:], 0.0, atol=1e-10)
 
