@@ -33,9 +33,13 @@ UNIT = "projections/s"
 WORKLOAD = dict(name="burgers_1d", family="B", B=512, nx=128, nt=100, seed=1001)
 H_TOL = 1e-8
 ROTATE = 4
-KERNEL = "k1d_mixed"                                   # dominant kernel of a step
-KERNEL_SOURCES = ("paper_2607_00095_b300/csrc/kern_1d_mixed.cu", "paper_2607_00095_b300/csrc/slice_newton.cuh",
-                  "paper_2607_00095_b300/csrc/df64.cuh", "paper_2607_00095_b300/csrc/snap_internal.h")
+# the forward path's tile kernel (moments, slice solves, write-back; the prepare and
+# statistics kernels around it overlap it by programmatic dependent launch)
+KERNELS = ("k1d_mixed",)
+KERNEL = "+".join(KERNELS)
+KERNEL_SOURCES = ("paper_2607_00095_b300/csrc/kern_1d_mixed.cu", "paper_2607_00095_b300/csrc/tile_1d.cuh",
+                  "paper_2607_00095_b300/csrc/slice_newton.cuh", "paper_2607_00095_b300/csrc/df64.cuh",
+                  "paper_2607_00095_b300/csrc/snap_internal.h")
 
 
 def parse():
@@ -147,6 +151,40 @@ def sources_digest(sources):
     return h.hexdigest()
 
 
+def link_ceiling(uh_h, pr_h, u_h, lam_h, st_h, d_in, d_out, reps):
+    """Plain pinned-memory copies of one step's bytes: host -> device alone, device -> host
+    alone, and both directions at once on two streams (ms per step and GB/s)."""
+    import torch
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def up():
+        with torch.cuda.stream(s1):
+            d_in[0].copy_(uh_h, non_blocking=True)
+            d_in[1].copy_(pr_h, non_blocking=True)
+
+    def down():
+        with torch.cuda.stream(s2):
+            u_h.copy_(d_out[0], non_blocking=True)
+            lam_h.copy_(d_out[1], non_blocking=True)
+            st_h.copy_(d_out[2], non_blocking=True)
+
+    def timed(fns):
+        for f in fns:
+            f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for f in fns:
+                f()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3 / reps
+
+    up_ms, down_ms, both_ms = timed([up]), timed([down]), timed([up, down])
+    h2d = uh_h.numel() * 8 + pr_h.numel() * 8
+    d2h = u_h.numel() * 8 + lam_h.numel() * 8 + st_h.numel()
+    return {"h2d_gbs": h2d / (up_ms * 1e6), "d2h_gbs": d2h / (down_ms * 1e6), "both_ms": both_ms}
+
+
 def kernel_traffic(name, sources):
     """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
     path = os.path.join(ROOT, "profiles", f"{name}_traffic.json")
@@ -233,7 +271,8 @@ def run_ours(args, rank, world, local):
                           "pcfm": measure_pcfm(dev),
                           "vorticity_2d": measure_vorticity(dev, hbm0),
                           "burgers_bc_1d": measure_burgers_bc(dev, hbm0),
-                          "burgers_flux_1d": measure_burgers_flux(dev, hbm0, 5)}), flush=True)
+                          "burgers_flux_1d": measure_burgers_flux(dev, hbm0, 5),
+                          "heat2_1d": measure_heat(dev, hbm0)}), flush=True)
         return 0
     w = WORKLOAD
     B, nx, nt = w["B"], w["nx"], w["nt"]
@@ -286,7 +325,9 @@ def run_ours(args, rank, world, local):
     e1.record()
     torch.cuda.synchronize()
     eager_ms = e0.elapsed_time(e1) / args.steps
-    k_ms, k_n = api.profile_read(KERNEL)
+    k_parts = {name: api.profile_read(name) for name in KERNELS}
+    k_ms = sum(ms for ms, _ in k_parts.values())
+    k_n = min(n for _, n in k_parts.values())
     api.profile_enable(0)
     api.profile_reset()
 
@@ -369,6 +410,7 @@ def run_ours(args, rank, world, local):
         uh_h = torch.as_tensor(host0[0].reshape(B, -1)).pin_memory()
         pr_h = torch.as_tensor(host0[1]).pin_memory()
         u_h = [torch.empty_like(uh_h).pin_memory() for _ in range(NS)]
+        lam_h = [torch.empty(B, p.n_rows, dtype=torch.float64).pin_memory() for _ in range(NS)]
         st_h = [torch.empty(B, 40, dtype=torch.uint8).pin_memory() for _ in range(NS)]
         d_in = [(torch.empty_like(d_uh), torch.empty_like(d_pr)) for _ in range(NS)]
         d_out = [(torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
@@ -397,6 +439,7 @@ def run_ours(args, rank, world, local):
             with torch.cuda.stream(s_out):
                 s_out.wait_event(ev_c[j])
                 u_h[j].copy_(d_out[j][0], non_blocking=True)
+                lam_h[j].copy_(d_out[j][1], non_blocking=True)
                 st_h[j].copy_(d_out[j][2], non_blocking=True)
                 ev_out[j].record(s_out)
 
@@ -416,10 +459,17 @@ def run_ours(args, rank, world, local):
         e2e_ms = a.elapsed_time(b) / n_e2e
         st = np.frombuffer(st_h[(n_e2e - 1) % NS].numpy().tobytes(), dtype=api.STATS_DTYPE)
         conv_e2e = int(((st["status"] == 0) & (st["h_inf"] <= H_TOL)).sum())
+        h2d = int(uh_h.numel() * 8 + pr_h.numel() * 8)
+        d2h = int(u_h[0].numel() * 8 + lam_h[0].numel() * 8 + st_h[0].numel())
+        # the link itself: the same bytes moved by plain pinned copies, each direction alone
+        # and both at once (the ceiling an end-to-end step can reach)
+        link = link_ceiling(uh_h, pr_h, u_h[0], lam_h[0], st_h[0], d_in[0], d_out[0], n_e2e)
         e2e = {"value": conv_e2e * world / (e2e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(uh_h.numel() * 8 + pr_h.numel() * 8),
-               "d2h_bytes_per_step": int(u_h[0].numel() * 8 + st_h[0].numel()),
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": e2e_ms,
+               "link_gbs_h2d": link["h2d_gbs"], "link_gbs_d2h": link["d2h_gbs"],
+               "link_ms_both": link["both_ms"],
+               "link_frac": link["both_ms"] / e2e_ms,
                "pipeline": "3 buffer sets: upload / project / download of consecutive steps overlap"}
 
     peaks = measured_peaks()
@@ -442,6 +492,7 @@ def run_ours(args, rank, world, local):
         extra["burgers_bc_1d"] = measure_burgers_bc(dev, hbm)
         extra["burgers_flux_1d"] = measure_burgers_flux(dev, hbm, 5)
         extra["burgers_flux10_1d"] = measure_burgers_flux(dev, hbm, 10)
+        extra["heat2_1d"] = measure_heat(dev, hbm)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -469,6 +520,7 @@ def run_ours(args, rank, world, local):
             "roofline": {"bound": "hbm", "kernel": KERNEL, "achieved": achieved, "peak": hbm,
                          "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                          "algorithmic_bytes_per_launch": launch_bytes, "kernel_ms": k_avg_ms,
+                         "kernel_ms_parts": {n: ms / max(c, 1) for n, (ms, c) in k_parts.items()},
                          "peak_source": peak_src},
             "fp64_fma_per_s": fp64,
             "cpu_baseline": cpu,
@@ -747,6 +799,85 @@ def measure_burgers_flux(dev, hbm, K, reps=50):
             "kernel_ms": kavg, "hbm_frac_of_measured": bytes_per_call / (kavg / 1e3) / 1e9 / hbm,
             "algorithmic_bytes_per_call": bytes_per_call, "backward_kernel_ms": bavg,
             "adjoint_forward_ratio": bavg / kavg}
+
+
+def measure_heat(dev, hbm, reps=30):
+    """Family F, the heat problem's second constraint regime (IC, mass, Crank-Nicolson PDE
+    residual, energy evolution): B = 512 samples of nx = nt = 100; four rotating sets, CUDA
+    graphs.  Forward (u by the time chain, lambda by backward substitution, statistics) and
+    the adjoint (dL/d(g, alpha)) kernel times."""
+    import torch
+
+    from paper_2607_00095_b300 import Problem, api, decode_stats, synthetic
+    w = synthetic.WORKLOADS["heat2_1d"]
+    B, nx, nt = w["B"], w["nx"], w["nt"]
+    p = Problem("F", nx, nt)
+    sets = []
+    for r in range(4):
+        uh, pr = synthetic.gen_heat(w["seed"] + 7919 * r, B, nx, nt)
+        d_uh = torch.as_tensor(uh.reshape(B, -1), device=dev)
+        d_pr = torch.as_tensor(pr, device=dev)
+        out = (torch.empty_like(d_uh), torch.empty(B, p.n_rows, dtype=torch.float64, device=dev),
+               torch.empty(B, 40, dtype=torch.uint8, device=dev))
+        sets.append((d_uh, d_pr, out))
+    for d_uh, d_pr, out in sets:
+        p.project(d_uh, d_pr, out=out)
+    torch.cuda.synchronize()
+    api.profile_reset()
+    api.profile_enable(1)
+    for i in range(8):
+        d_uh, d_pr, out = sets[i % 4]
+        p.project(d_uh, d_pr, out=out)
+    torch.cuda.synchronize()
+    k_ms, k_n = api.profile_read("k_heat_forward")
+    api.profile_enable(0)
+    api.profile_reset()
+    cap = torch.cuda.Stream()
+    graphs = []
+    with torch.cuda.stream(cap):
+        for d_uh, d_pr, out in sets:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap):
+                p.project(d_uh, d_pr, out=out, stream=cap)
+            graphs.append(g)
+    for g in graphs:
+        g.replay()
+    it = [0]
+
+    def step():
+        graphs[it[0] % 4].replay()
+        it[0] += 1
+    ms = _event_ms(step, reps)
+    conv = 0
+    for d_uh, d_pr, out in sets:
+        _, hinf = p.residual(out[0], d_pr, want_rows=False)
+        st = decode_stats(out[2])
+        conv += int(((st["status"] == 0) & (hinf.cpu().numpy() <= H_TOL)).sum())
+    conv /= 4
+    bytes_per_call = (8 * (2 * p.n_vars + p.n_rows + p.n_params) + 40) * B
+    kavg = k_ms / max(k_n, 1)
+    gbar = torch.as_tensor(synthetic.gen_gbar(w["seed"] + 1, (B, p.n_vars)), device=dev)
+    d_uh, d_pr, out = sets[0]
+    for _ in range(3):
+        p.backward(gbar, out[0], out[1], d_pr, stats=out[2])
+    torch.cuda.synchronize()
+    api.profile_reset()
+    api.profile_enable(1)
+    for _ in range(8):
+        p.backward(gbar, out[0], out[1], d_pr, stats=out[2])
+    torch.cuda.synchronize()
+    b_ms, b_n = api.profile_read("k_heat_backward")
+    api.profile_enable(0)
+    api.profile_reset()
+    bavg = b_ms / max(b_n, 1)
+    fp64_ops = B * nt * nx * 2 * 12           # two time chains, ~12 FP64 operations per element
+    return {"workload": "heat2_1d", "B": B, "nx": nx, "nt": nt, "ms_per_call": ms,
+            "converged_per_call": conv, "projections_per_s": conv / (ms / 1e3),
+            "kernel": "k_heat_forward", "kernel_ms": kavg,
+            "hbm_frac_of_measured": bytes_per_call / (kavg / 1e3) / 1e9 / hbm,
+            "algorithmic_bytes_per_call": bytes_per_call,
+            "fp64_ops_per_call_estimate": fp64_ops,
+            "backward_kernel_ms": bavg, "adjoint_forward_ratio": bavg / kavg}
 
 
 def measure_burgers_bc(dev, hbm, reps=50):

@@ -114,7 +114,23 @@ typedef enum {
    * The KKT point is evaluated directly (forward Godunov steps, backward substitution for
    * the multipliers; stats.iters = 1).  Adjoint: dL/du_hat is 0 on slices 0..K and
    * gbar - mean(gbar) on the others; grad_params = dL/dg.  u0 must be NULL. */
-  SNAP_FAMILY_E_BURGERS_FLUX = 5
+  SNAP_FAMILY_E_BURGERS_FLUX = 5,
+  /* Heat equation, second constraint regime (Appendix A "Heat Equation Problems"; the
+   * energy-evolution identity of the appendix "Energy Evolution Constraint"): 1-D field on
+   * the periodic [0, 2 pi), x_i = i dx, dx = 2 pi / nx, t_k = k dt, dt = 1 / (nt - 1).  Rows,
+   * in this order: IC u^0_i = g_i (nx); mass dx sum_i u^k_i = dx sum_i g_i (nt); PDE residual
+   * (u^k_i - u^{k-1}_i) / dt - alpha/2 (D2 u^k + D2 u^{k-1})_i, k = 1..nt-1 (Crank-Nicolson,
+   * (nt - 1) nx rows, slice-major; D2 the periodic second difference / dx^2); energy
+   * evolution (E^k - E^{k-1}) / dt + alpha dx sum_i ((ubar_{i+1} - ubar_i) / dx)^2,
+   * E^k = 1/2 dx sum_i (u^k_i)^2, ubar = (u^k + u^{k-1}) / 2, k = 1..nt-1 (nt - 1 rows).  The
+   * mass and energy rows are implied by the IC and PDE rows (summation by parts: lambda 0,
+   * counted in h_inf); the active rows are square, so the projection is the Crank-Nicolson
+   * solution from g for every u_hat, and lambda solves J^T lambda = u_hat - u (backward
+   * substitution in time; stats.iters = 1, kkt_inf = the largest active-row residual).
+   * params[b] = {g_0..g_{nx-1}, alpha}, alpha >= 0 (else INFEASIBLE_PARAMS); nx in [3, 512];
+   * desc.rows must be 0; u0 must be NULL.  Adjoint: dL/du_hat = 0, grad_params = dL/d(g,
+   * alpha).  No workspace. */
+  SNAP_FAMILY_F_HEAT_ENERGY = 6
 } snap_family;
 
 /* Row-type bits for snap_problem_desc.rows (1-D families). */
@@ -135,8 +151,10 @@ enum {
   SNAP_SAMPLE_RESIDUAL = 5,          /* KKT converged but some nominal row (one left out of
                                         the solve) has |h| > tol_h: inconsistent params */
   SNAP_SAMPLE_SINGULAR = 6,          /* singular Newton-KKT matrix */
-  SNAP_SAMPLE_NOT_MINIMUM = 7        /* converged to a KKT point whose KKT matrix has the
+  SNAP_SAMPLE_NOT_MINIMUM = 7,       /* converged to a KKT point whose KKT matrix has the
                                         wrong inertia (second-order condition fails) */
+  SNAP_SAMPLE_DEVICE_WAIT = 8        /* a bounded wait inside a kernel ran out (an asynchronous
+                                        copy did not complete): the slice was not solved */
 };
 
 /* Solver paths for snap_options.path. */
@@ -192,6 +210,14 @@ typedef struct {
   double w_keep;       /* each step keeps every diagonal entry of W at >= w_keep times its
                           current value (default 0.01; 0 disables) */
 } snap_options;
+
+/* Bounds-checked build (library libsnap_bc.so, compiled with -DSNAP_BOUNDS_CHECK): the
+ * kernels' indexed global accesses are checked against their arrays' extents; the first
+ * failing access is recorded in a device error word (bits 63..48: the access site, bits
+ * 47..0: the index) and skipped instead of trapping.  Writes the word to *word (0: no
+ * failure) and clears it when clear != 0; synchronous.  The paper has no counterpart: this is
+ * a diagnostic build.  Errors: UNSUPPORTED in the normal build (word set to 0), CUDA. */
+SNAP_API snap_status snap_bounds_error(unsigned long long *word, int clear);
 
 /* Message of the last failed call on this host thread ("" if none).  Never NULL. */
 SNAP_API const char *snap_last_error(void);

@@ -9,11 +9,11 @@ SNAP_OK = 0
 NOALLOC_SCRATCH_BYTES = 8388608
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NO_MEMORY",
                 5: "WORKSPACE", 6: "NOT_READY"}
-FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY, FAMILY_D, FAMILY_E = 0, 1, 2, 3, 4, 5
+FAMILY_A, FAMILY_B, FAMILY_C, FAMILY_TOY, FAMILY_D, FAMILY_E, FAMILY_F = 0, 1, 2, 3, 4, 5, 6
 ROW_IC, ROW_MASS, ROW_ENERGY, ROW_BOUNDARY = 1, 2, 4, 8
 PATH_AUTO, PATH_GENERAL, PATH_MOMENT, PATH_MIXED = 0, 1, 2, 3
 SAMPLE_STATUS = {0: "OK", 1: "MAXITER", 2: "LINESEARCH", 3: "NONFINITE", 4: "INFEASIBLE_PARAMS",
-                 5: "RESIDUAL", 6: "SINGULAR", 7: "NOT_MINIMUM"}
+                 5: "RESIDUAL", 6: "SINGULAR", 7: "NOT_MINIMUM", 8: "DEVICE_WAIT"}
 
 
 class ProblemDesc(C.Structure):
@@ -53,6 +53,7 @@ _lib = None
 _vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
 _PROTOS = {
     "snap_last_error": (C.c_char_p, []),
+    "snap_bounds_error": (C.c_int, [C.POINTER(C.c_ulonglong), C.c_int]),
     "snap_version": (C.c_char_p, []),
     "snap_options_default": (C.c_int, [C.POINTER(Options)]),
     "snap_problem_create": (C.c_int, [C.POINTER(ProblemDesc), C.POINTER(_vp)]),

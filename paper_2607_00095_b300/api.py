@@ -16,7 +16,7 @@ STATS_DTYPE = np.dtype([("iters", "<i4"), ("backtracks", "<i4"), ("status", "<i4
                         ("corrections", "<i4"), ("h_inf", "<f8"), ("kkt_inf", "<f8"),
                         ("obj", "<f8")])
 FAMILIES = {"A": _abi.FAMILY_A, "B": _abi.FAMILY_B, "C": _abi.FAMILY_C, "toy": _abi.FAMILY_TOY,
-            "D": _abi.FAMILY_D, "E": _abi.FAMILY_E}
+            "D": _abi.FAMILY_D, "E": _abi.FAMILY_E, "F": _abi.FAMILY_F}
 PATHS = {"auto": _abi.PATH_AUTO, "general": _abi.PATH_GENERAL, "moment": _abi.PATH_MOMENT,
          "mixed": _abi.PATH_MIXED}
 

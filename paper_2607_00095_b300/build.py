@@ -22,33 +22,42 @@ def deps():
                               + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in deps())
 
 
-def build(force=False, verbose=False):
-    if not force and up_to_date():
-        return LIB
+LIB_BC = os.path.join(HERE, "libsnap_bc.so")
+
+
+def build(force=False, verbose=False, bounds_check=False):
+    """libsnap.so, or with bounds_check the diagnostic libsnap_bc.so (-DSNAP_BOUNDS_CHECK:
+    indexed accesses record an error word instead of faulting)."""
+    lib = LIB_BC if bounds_check else LIB
+    if not force and up_to_date(lib):
+        return lib
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    objdir = os.path.join(HERE, "_build")
+    objdir = os.path.join(HERE, "_build_bc" if bounds_check else "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [nvcc, *NVCC_FLAGS, "-I", INCLUDE, "-dc", src, "-o", obj]
+        if bounds_check:
+            cmd.insert(1, "-DSNAP_BOUNDS_CHECK")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         subprocess.check_call(cmd)
         objs.append(obj)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs,
                            "-o", tmp, "-lcudart"])
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                bounds_check="--bounds-check" in sys.argv))

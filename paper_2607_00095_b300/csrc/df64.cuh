@@ -177,6 +177,47 @@ DF_INL bool df_split(double x, float &h, float &l) {
   return zero || (e - 949u) <= (1080u - 949u);
 }
 
+// Split without any conversion instruction (integer operations and one FP32 add and multiply
+// only, so that it keeps off the FP64 pipe, which also executes the double -> float
+// conversion): h = x truncated to 24 significant bits; the 29 remaining mantissa bits D are an
+// integer multiple of ulp(x); their top 23 bits D >> 6 become an exact float through the 2^23
+// bias and are scaled by 2^6 ulp(x).  |x - h - l| < 2^-46 |x| and |l| < ulp(h).  Same range
+// and return value as df_split.
+DF_INL bool df_split_trunc(double x, float &h, float &l) {
+  const unsigned hw = df_hiword(x);
+  const unsigned lw = df_loword(x);
+  const unsigned e = (hw >> 20) & 0x7FFu;
+  const unsigned sgn = hw & 0x80000000u;
+  h = df_bitsf(sgn | ((e - 896u) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+  const float f = df_bitsf(0x4B000000u | ((lw & 0x1FFFFFFFu) >> 6)) - 8388608.0f;
+  l = f * df_bitsf(sgn | ((e - 942u) << 23));
+  const bool zero = ((hw & 0x7FFFFFFFu) | lw) == 0u;
+  const bool ok = zero || (e - 949u) <= (1080u - 949u);
+  if (!ok || zero) { h = 0.0f; l = 0.0f; }
+  return ok;
+}
+
+// The same truncating split in fewer operations, for the streaming moment pass: a funnel shift
+// places the double's exponent and leading 23 mantissa bits in float position (the exponent
+// rebias 1023 -> 127 is a flip of bit 30 for exponents in range), and l is scaled by
+// 2^-46 times the power of two of h.  Zero (and every value outside [2^-74, 2^57]) returns
+// false with h, l unspecified: the caller takes its FP64 path for that row.
+DF_INL bool df_split_trunc_fast(double x, float &h, float &l) {
+  const unsigned hw = df_hiword(x);
+  const unsigned lw = df_loword(x);
+  const unsigned e = (hw >> 20) & 0x7FFu;
+#ifdef __CUDA_ARCH__
+  const unsigned f = __funnelshift_l(lw, hw, 3);
+#else
+  const unsigned f = (hw << 3) | (lw >> 29);
+#endif
+  const unsigned hb = (((f & 0x7FFFFFFFu) ^ 0x40000000u)) | (hw & 0x80000000u);
+  h = df_bitsf(hb);
+  const float fl = df_bitsf(0x4B000000u | ((lw & 0x1FFFFFFFu) >> 6)) - 8388608.0f;
+  l = fl * df_bitsf((hb & 0xFF800000u) - (46u << 23));
+  return (e - 949u) <= (1080u - 949u);
+}
+
 // float -> double by integer bit construction (normal floats and zero; other values go
 // through the conversion instruction)
 DF_INL double df_f2d(float f) {

@@ -197,6 +197,105 @@ __device__ void fd_solve_tiled(float *rf, float *tf, const float *Q, const float
   __syncthreads();
 }
 
+// Tensor-core form of the class solve for M = 32 (the 64 x 64 frames): the same four products
+// C = X^T Y (C[m][n] = sum_k X[k][m] Y[k][n], X and Y row-major M x M in shared memory) as
+// warp-level mma.sync m16n8k8 with TF32 operands and FP32 accumulation.  Every operand is
+// split into two TF32 values, x = x_big + x_small (x_small = tf32(x - x_big)), and a product
+// is accumulated as x_small y_big + x_big y_small + x_big y_big, which keeps about the
+// accuracy of the FP32 products (the dropped x_small y_small is below 2^-22 relative); the
+// double-float refinement against the exact stencil residual is unchanged.  Eight warps:
+// warp w computes rows 16 (w & 1) .. + 15 of the output of class w >> 1, all 32 columns.
+__device__ __forceinline__ uint32_t fd_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void fd_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
+                                       uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// acc[nt][.] = the 16 x 8 output tiles (rows m0 .. m0 + 15, columns 8 nt ..) of X^T Y, M = 32
+__device__ __forceinline__ void fd_xty32(const float *X, const float *Y, int m0,
+                                         float (&acc)[4][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[nt][e] = 0.0f;
+#pragma unroll
+  for (int k0 = 0; k0 < 32; k0 += 8) {
+    // A = X^T: a0 (m0+g, k0+t), a1 (m0+g+8, k0+t), a2 (m0+g, k0+t+4), a3 (m0+g+8, k0+t+4)
+    const float af[4] = {X[(k0 + t) * 32 + m0 + g], X[(k0 + t) * 32 + m0 + g + 8],
+                         X[(k0 + t + 4) * 32 + m0 + g], X[(k0 + t + 4) * 32 + m0 + g + 8]};
+    uint32_t ab[4], as[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ab[e] = fd_tf32(af[e]);
+      as[e] = fd_tf32(af[e] - __uint_as_float(ab[e]));
+    }
+#pragma unroll
+    for (int nt = 0; nt < 4; ++nt) {
+      // B = Y: b0 (k0+t, 8 nt + g), b1 (k0+t+4, 8 nt + g)
+      const float y0 = Y[(k0 + t) * 32 + 8 * nt + g], y1 = Y[(k0 + t + 4) * 32 + 8 * nt + g];
+      const uint32_t bb0 = fd_tf32(y0), bb1 = fd_tf32(y1);
+      const uint32_t bs0 = fd_tf32(y0 - __uint_as_float(bb0));
+      const uint32_t bs1 = fd_tf32(y1 - __uint_as_float(bb1));
+      fd_mma(acc[nt], as, bb0, bb1);
+      fd_mma(acc[nt], ab, bs0, bs1);
+      fd_mma(acc[nt], ab, bb0, bb1);
+    }
+  }
+}
+
+// out[m][n] (row-major, M = 32) from the accumulators of fd_xty32, times scale[m][n] if given
+__device__ __forceinline__ void fd_store32(float *out, const float (&acc)[4][4], int m0,
+                                           const float *scale) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < 4; ++nt) {
+    const int n = 8 * nt + 2 * t;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + g + 8 * h;
+      float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
+      if (scale) { v0 *= scale[m * 32 + n]; v1 *= scale[m * 32 + n + 1]; }
+      out[m * 32 + n] = v0;
+      out[m * 32 + n + 1] = v1;
+    }
+  }
+}
+
+__device__ void fd_solve_mma32(float *rf, float *tf, const float *Q, const float *Qt,
+                               const float *inv) {
+  constexpr int MM = 32 * 32;
+  const int w = threadIdx.x >> 5, c = w >> 1, m0 = 16 * (w & 1);
+  float acc[4][4];
+  // T = Q^T R, kept as Tt = T^T = R^T Q
+  fd_xty32(rf + c * MM, Q, m0, acc);
+  __syncthreads();
+  fd_store32(tf + c * MM, acc, m0, nullptr);
+  __syncthreads();
+  // R = (T Q) .* inv = (Tt^T Q) .* inv
+  fd_xty32(tf + c * MM, Q, m0, acc);
+  fd_store32(rf + c * MM, acc, m0, inv);
+  __syncthreads();
+  // T = Q R, kept as T3t = (Q R)^T = R^T Q^T
+  fd_xty32(rf + c * MM, Qt, m0, acc);
+  __syncthreads();
+  fd_store32(tf + c * MM, acc, m0, nullptr);
+  __syncthreads();
+  // R = T Q^T = T3t^T Q^T
+  fd_xty32(tf + c * MM, Qt, m0, acc);
+  fd_store32(rf + c * MM, acc, m0, nullptr);
+  __syncthreads();
+}
+
 // class / class-local coordinates of cell (i, j) of an N = 2M grid
 template <int M>
 __device__ __forceinline__ int cell_slot(int i, int j) {
@@ -330,7 +429,8 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
   __syncthreads();
   const df64 inv_scale = df64(1.0f, 0.0f) / scale;
   for (int round = 0; round < REFINE; ++round) {
-    if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
+    if constexpr (M == 32) fd_solve_mma32(v.Rf, v.Tf, v.Q, v.Qt, v.I);
+    else if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
     else fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
     for (int s = threadIdx.x; s < NN; s += T2D) {
       const df64 zz = v.z(s) + scale * df64(v.Rf[s], 0.0f);

@@ -20,6 +20,7 @@
 #include <math.h>
 #include <stdint.h>
 
+
 #include "sample_1d.cuh"
 #include "slice_newton.cuh"
 #include "snap_internal.h"
@@ -484,6 +485,9 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
     const int m_present = ((g.rows & SL_MASS) != 0) + ((g.rows & SL_ENERGY) != 0) +
                           ((g.rows & SL_BOUND) != 0);
     double lm = 0.0, le = 0.0, lbd = 0.0;
+    // an explicit start point takes the primal-dual iteration; the start u_hat keeps the
+    // iterates stationary in u (u = argmin L(., lambda)), as the moment paths do
+    const bool restore = (u0 == nullptr);
     double G[NPL];
     GenEval<NPL> e;
     gen_eval<NPL>(g, d, U, H, lm, le, lbd, G, e, lane);
@@ -491,10 +495,19 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
     const bool infeasible = ((g.rows & SL_BOUND) && d.C < 0.0) ||
                             ((g.rows & SL_ENERGY) && d.E < ((g.rows & SL_MASS) ? d.M * d.M : 0.0));
     if (infeasible) status = SNAP_SAMPLE_INFEASIBLE_PARAMS;
+    // polish: after the stopping test one more full Newton step, kept when ||F||_inf does not
+    // increase (the multipliers of ill-conditioned slices to the rounding level)
+    bool polish = false;
     for (int it = 0; !infeasible; ++it) {
       if (!(e.res == e.res) || isinf(e.res)) { status = SNAP_SAMPLE_NONFINITE; break; }
-      if (e.res <= o.tol_kkt) { status = SNAP_SAMPLE_OK; break; }
-      if (it >= o.max_iter) { status = SNAP_SAMPLE_MAXITER; break; }
+      if (e.res <= o.tol_kkt) {
+        status = SNAP_SAMPLE_OK;
+        if (polish) break;
+        polish = true;
+      } else if (polish) {
+        break;
+      }
+      if (!polish && it >= o.max_iter) { status = SNAP_SAMPLE_MAXITER; break; }
       double delta = 0.0, w = e.alpha, wb = e.beta;
       double s00, s01, s02, s11, s12, s22, v0, v1, v2;
       Ldl3<double> f;
@@ -511,7 +524,10 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
         delta = (delta == 0.0) ? o.delta0 : delta * 10.0;
         ncorr++;
       }
-      if (!ok) { status = SNAP_SAMPLE_SINGULAR; break; }
+      if (!ok) {
+        if (!polish) status = SNAP_SAMPLE_SINGULAR;
+        break;
+      }
       double dlm, dle, dlb;
       ldl3_solve(f, (g.rows & SL_MASS) ? e.hm - v0 : 0.0, (g.rows & SL_ENERGY) ? e.he - v1 : 0.0,
                  (g.rows & SL_BOUND) ? e.hb - v2 : 0.0, dlm, dle, dlb);
@@ -525,7 +541,7 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
         if (i >= nx) dU[j] = 0.0;
       }
       double t = 1.0;
-      if (o.w_keep > 0.0) {
+      if (o.w_keep > 0.0 && !polish) {
         const double da = (g.rows & SL_ENERGY) ? 2.0 * g.dx * dle : 0.0;
         const double db = da + 2.0 * dlb;
         if (e.alpha > 0.0 && da < 0.0) t = fmin(t, (1.0 - o.w_keep) * e.alpha / (-da));
@@ -536,23 +552,42 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
       double Ut[NPL], Gt[NPL];
       GenEval<NPL> et;
       for (;;) {
+        if (restore) {
+          // start at u_hat: trial points keep grad_u L = 0, u = (u_hat - dx lam_m 1) / W
+          const double lmt = lm + t * dlm;
+          const double alt = 1.0 + 2.0 * g.dx * (le + t * dle);
+          const double bet = alt + 2.0 * (lbd + t * dlb);
 #pragma unroll
-        for (int j = 0; j < NPL; ++j) Ut[j] = U[j] + t * dU[j];
+          for (int j = 0; j < NPL; ++j) {
+            const int i = lane + 32 * j;
+            Ut[j] = (i < nx) ? (H[j] - g.dx * lmt) / ((i == 0 || i == g.ih) ? bet : alt) : 0.0;
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) Ut[j] = U[j] + t * dU[j];
+        }
         gen_eval<NPL>(g, d, Ut, H, lm + t * dlm, le + t * dle, lbd + t * dlb, Gt, et, lane);
+        if (polish) {
+          accepted = et.res <= e.res && et.alpha > 0.0 && et.beta > 0.0;
+          break;
+        }
         if (et.phi <= (1.0 - 2.0 * o.c1 * t) * e.phi) { accepted = true; break; }
         if (nb >= o.max_backtracks) break;
         nb++;
         t *= 0.5;
       }
       nbt += nb;
-      if (!accepted) { status = SNAP_SAMPLE_LINESEARCH; break; }
+      if (!accepted) {
+        if (!polish) status = SNAP_SAMPLE_LINESEARCH;
+        break;
+      }
 #pragma unroll
       for (int j = 0; j < NPL; ++j) { U[j] = Ut[j]; G[j] = Gt[j]; }
       lm += t * dlm;
       le += t * dle;
       lbd += t * dlb;
       e = et;
-      iters = it + 1;
+      if (!polish) iters = it + 1;     // the polishing step is not counted
     }
     if (status == SNAP_SAMPLE_OK) {
       // second-order sufficient condition at the converged point
@@ -771,6 +806,7 @@ size_t ws_bytes_1d(const snap_problem *p, int B) {
 }
 
 static int warps_blocks(int nwarps) { return (nwarps * 32 + 127) / 128; }
+
 
 cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
                               const double *params, const double *u0, double *u, double *lambda,

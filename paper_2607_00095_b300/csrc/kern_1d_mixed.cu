@@ -6,15 +6,16 @@
 // write-back u_i = a u_hat_i + c) and moves everything else to the FP32 / integer pipes:
 //
 //   phase 1  (4 lanes per slice, 8 slices per warp instruction, 16-byte loads): every
-//            u_hat_i is split into a float pair hi + lo with integer operations and one
-//            conversion (|u_hat - hi - lo| <= 2^-48 |u_hat|), and the interior moments
+//            u_hat_i is split into a float pair hi + lo with integer operations only
+//            (df_split_trunc_fast: nothing on the FP64 pipe; |u_hat - hi - lo| < 2^-46
+//            |u_hat|), and the interior moments
 //            S1 = sum u_hat_i, S2 = sum u_hat_i^2 are accumulated in double-float
 //            (error-free TwoSum / TwoProd), reduced across the 4 lanes with two butterfly
 //            steps;
 //   phase 2  (one slice per lane): the slice's Newton-KKT iteration in moment form,
 //            first in float, then in double-float to the FP64 stopping tolerance
-//            (slice_solve_mixed); E_k = E0 q^k with q = exp(-r dt) by binary powering in
-//            double-float;
+//            (t1_solve_slice / slice_solve_mixed, warm-started inside W > 0); E_k = E0 q^k
+//            with q = exp(-r dt) by binary powering in double-float;
 //   phase 3  (4 lanes per slice): u = fma(a, u_hat, c) in FP64, 16-byte stores.
 //
 // The IC slices (k = 0) are solved by the per-sample prepare kernel (k1d_params), a full
@@ -26,17 +27,18 @@
 // kernel in turn lets the statistics kernel launch early (it waits the same way).
 //
 // A slice whose values leave the range of the float-pair representation (|u_hat| outside
-// [2^-74, 2^57], or non-finite) falls back to FP64 moments and the FP64 iteration.
+// [2^-74, 2^57], exactly zero, or non-finite) falls back to FP64 moments and the FP64
+// iteration.
 //
-// The uneven-batch kernel runs the same three phases from tile_1d.cuh (slices located through
-// a per-instance pointer table).  This kernel keeps its own copy of the tile inside its
-// grid-stride loop: the same code moved into an inlined function measured 6-7 % slower here
-// (95 against 89 us per B=512 Burgers launch on B300), so the hot path stays as written.
+// Phase 2 is t1_solve_slice (tile_1d.cuh), the same device code as the uneven-batch kernel's
+// tile; phases 1 and 3 stay inline here (the batch kernel locates its slices through a
+// per-instance pointer table instead).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
-#include "slice_newton.cuh"
+#include "snap_bounds.cuh"
+#include "tile_1d.cuh"
 #include "snap_internal.h"
 
 namespace {
@@ -44,19 +46,6 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 
 enum { KIND_MOMENT = 0, KIND_NONE = 3 };
-
-__device__ __forceinline__ double nan_max(double a, double b) { return (a < b || b != b) ? b : a; }
-
-// x^k for k >= 0 by binary powering in double-float
-__device__ __forceinline__ df64 df_pow(df64 x, int k) {
-  df64 r(1.0f, 0.0f);
-  while (k > 0) {
-    if (k & 1) r = r * x;
-    x = x * x;
-    k >>= 1;
-  }
-  return r;
-}
 
 __device__ __forceinline__ df64 shfl_df(df64 v, int off) {
   return df64(__shfl_xor_sync(FULL, v.hi, off), __shfl_xor_sync(FULL, v.lo, off));
@@ -112,15 +101,16 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
               const int i = i0 + 8 * c;
-              v[c] = (i < nx) ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
+              v[c] = (i < nx && snap_in_bounds(SNAP_SITE_MOMENT_ROW, s * nx + i + 1, total * nx))
+                         ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
             }
 #pragma unroll
             for (int c = 0; c < CH; ++c) {
               const int i = i0 + 8 * c;
               if (i >= nx) break;
               float h0, l0, h1, l1;
-              ok &= df_split(v[c].x, h0, l0);
-              ok &= df_split(v[c].y, h1, l1);
+              ok &= df_split_trunc_fast(v[c].x, h0, l0);
+              ok &= df_split_trunc_fast(v[c].y, h1, l1);
               if (i == 0 || i == ih) { h0 = 0.0f; l0 = 0.0f; }
               if (i + 1 == ih) { h1 = 0.0f; l1 = 0.0f; }
               else { pmx = fmaxf(pmx, h1); pmn = fminf(pmn, h1); }
@@ -173,159 +163,15 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
     const long long s = sbase + 8 * r + q;
     int kind = KIND_NONE;
     double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
-    if (s < total) {
+    if (s < total && (s % g.nt) != 0 && snap_in_bounds(SNAP_SITE_MIXED_ROW, s, total)) {
+      // the IC slice (k = 0) is written by the prepare kernel
       const int b = (int)(s / g.nt);
       const int k = (int)(s % g.nt);
-      const double *pg = params + (size_t)b * g.n_params;
-      double *lb = lam + (size_t)b * g.n_rows;
       const double *row = uh + (size_t)s * nx;
-      const SampleDerived dv = sd[b];
-      BlockStat st;
-      if (k == 0) {
-        // IC slice: written by the prepare kernel
-      } else {
-        kind = KIND_MOMENT;
-        const double uh0 = row[0], uhh = row[ih];
-        const double C = (g.rows & SL_BOUND) ? pg[g.p_c + k] : 0.0;
-        double hm, he, hb, res, S1d, S2d;
-        SliceResult R;
-        double lmd, led, lbd;
-        float u0h, u0l, uhh_h, uhh_l, ch, cl;
-        const bool range_ok = mok && df_split(uh0, u0h, u0l) && df_split(uhh, uhh_h, uhh_l) &&
-                              df_split(C, ch, cl);
-        if (range_ok) {
-          SliceIn<df64> d;
-          d.S1 = m1; d.S2 = m2;
-          d.mx = df64(mmx, 0.0f); d.mn = df64(mmn, 0.0f);
-          d.uh0 = df64(u0h, u0l); d.uhh = df64(uhh_h, uhh_l);
-          d.n = df64((float)(nx - 2), 0.0f);
-          d.nint = nx - 2;
-          d.dx = dxd;
-          d.M = df64(dv.Mh, dv.Ml);
-          df64 E(0.0f, 0.0f);
-          if (g.rows & SL_ENERGY) {
-            const df64 e = df64(dv.E0h, dv.E0l) * df_pow(df64(dv.qh, dv.ql), k);
-            const df64 fl = df64(dv.fh, dv.fl);
-            E = (e >= fl) ? e : fl;
-          }
-          d.E = E;
-          d.C = df64(ch, cl);
-          d.rows = g.rows;
-          const df64 zero(0.0f, 0.0f);
-          const bool infeasible = ((g.rows & SL_BOUND) && ch < 0.0f) ||
-                                  ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? d.M * d.M : zero));
-          SliceZ<df64> z{df64(1.0f, 0.0f), zero, d.uh0, d.uhh, zero, zero, zero};
-          SliceEval<df64> e;
-          if (infeasible) {
-            slice_eval(d, z, e);
-            R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
-          } else {
-            R = slice_solve_mixed(d, z, e, o, so_f, so_d);
-          }
-          A = (double)z.a; Cc = (double)z.c; P0 = (double)z.p0; PH = (double)z.ph;
-          lmd = (double)z.lm; led = (double)z.le; lbd = (double)z.lb;
-          // statistics in double-float, one conversion each
-          const df64 hmx = sl_max(sl_max(sl_abs(e.hm), sl_abs(e.he)), sl_abs(e.hb));
-          const df64 am1 = z.a - df64(1.0f, 0.0f);
-          const df64 d0 = z.p0 - d.uh0, dh = z.ph - d.uhh;
-          const df64 obj = (am1 * am1 * d.S2 + df64(2.0f, 0.0f) * am1 * z.c * d.S1 + z.c * z.c * d.n +
-                            d0 * d0 + dh * dh) * df64(0.5f, 0.0f);
-          st.iters = R.iters;
-          st.backtracks = R.backtracks;
-          st.status = R.status;
-          st.corrections = R.corrections;
-          st.kkt_inf = (double)e.res;
-          st.h_inf = (double)hmx;
-          st.obj = (double)obj;
-          if (e.res != e.res) st.kkt_inf = NAN;
-          if (hmx != hmx) st.h_inf = NAN;
-          if (cache) {
-            const double al = (double)e.alpha, be = (double)e.beta;
-            S1d = (double)m1; S2d = (double)m2;
-            SliceIn<double> d64 = slice_in_cast<double>(d);
-            SliceZ<double> z64{A, Cc, P0, PH, lmd, led, lbd};
-            double s00, s01, s02, s11, s12, s22;
-            slice_schur(d64, z64, A * S1d + Cc * (double)(nx - 2),
-                        A * A * S2d + 2.0 * A * Cc * S1d + Cc * Cc * (double)(nx - 2), 1.0 / al,
-                        1.0 / be, s00, s01, s02, s11, s12, s22);
-            Ldl3<double> f;
-            if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-              f.d0 = f.d1 = f.d2 = 0.0;
-              f.l10 = f.l20 = f.l21 = 0.0;
-            }
-            SliceFactor sf{al, be, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-            cache[s] = sf;
-          }
-        } else {
-          // FP64 fallback: moments in FP64 by this lane, FP64 iteration
-          double a1 = 0.0, a2 = 0.0, mx = -INFINITY, mn = INFINITY;
-          for (int i = 0; i < nx; ++i) {
-            if (i == 0 || i == ih) continue;
-            const double v = row[i];
-            a1 += v;
-            a2 = fma(v, v, a2);
-            mx = fmax(mx, v);
-            mn = fmin(mn, v);
-            if (v != v) mx = v;
-          }
-          SliceIn<double> d;
-          d.S1 = a1; d.S2 = a2; d.mx = mx; d.mn = mn;
-          d.uh0 = uh0; d.uhh = uhh;
-          d.n = (double)(nx - 2);
-          d.nint = nx - 2;
-          d.dx = g.dx;
-          d.M = dv.M;
-          double E = 0.0;
-          if (g.rows & SL_ENERGY) {
-            const double e = dv.E0 * exp(-pg[g.p_rate] * ((double)k / (double)(g.nt - 1)));
-            const double fl = dv.M * dv.M + g.energy_floor;
-            E = e >= fl ? e : fl;
-          }
-          d.E = E;
-          d.C = C;
-          d.rows = g.rows;
-          const bool infeasible = ((g.rows & SL_BOUND) && C < 0.0) ||
-                                  ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? dv.M * dv.M : 0.0));
-          SliceZ<double> z{1.0, 0.0, uh0, uhh, 0.0, 0.0, 0.0};
-          SliceEval<double> e;
-          if (infeasible) {
-            slice_eval(d, z, e);
-            R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
-          } else {
-            R = slice_newton(d, z, e, o);
-          }
-          A = z.a; Cc = z.c; P0 = z.p0; PH = z.ph;
-          lmd = z.lm; led = z.le; lbd = z.lb;
-          hm = e.hm; he = e.he; hb = e.hb; res = e.res;
-          S1d = a1; S2d = a2;
-          if (cache) {
-            double s00, s01, s02, s11, s12, s22;
-            slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
-            Ldl3<double> f;
-            if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-              f.d0 = f.d1 = f.d2 = 0.0;
-              f.l10 = f.l20 = f.l21 = 0.0;
-            }
-            SliceFactor sf{e.alpha, e.beta, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-            cache[s] = sf;
-          }
-        }
-        if (!range_ok) {
-          st.iters = R.iters;
-          st.backtracks = R.backtracks;
-          st.status = R.status;
-          st.corrections = R.corrections;
-          st.kkt_inf = res;
-          st.h_inf = nan_max(nan_max(fabs(hm), fabs(he)), fabs(hb));
-          const double am1 = A - 1.0;
-          st.obj = 0.5 * (am1 * am1 * S2d + 2.0 * am1 * Cc * S1d + Cc * Cc * (double)(nx - 2) +
-                          (P0 - uh0) * (P0 - uh0) + (PH - uhh) * (PH - uhh));
-        }
-        if (g.off_mass >= 0) lb[g.off_mass + k] = lmd;
-        if (g.off_energy >= 0) lb[g.off_energy + k] = led;
-        if (g.off_bound >= 0) lb[g.off_bound + k] = lbd;
-        bst[s] = st;
-      }
+      kind = KIND_MOMENT;
+      t1_solve_slice(g, k, m1, m2, mmx, mmn, mok, __ldg(row), __ldg(row + ih), row,
+                     params + (size_t)b * g.n_params, sd[b], lam + (size_t)b * g.n_rows, bst + s,
+                     cache ? cache + s : nullptr, o, so_f, so_d, dxd, A, Cc, P0, PH);
     }
     // ---------------- phase 3: write-back, 4 lanes per slice ----------------
 #pragma unroll 1
@@ -347,7 +193,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
             const int i = i0 + 8 * c;
-            v[c] = (i < nx) ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
+            v[c] = (i < nx) ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
           }
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
@@ -356,7 +202,8 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
             double2 w;
             w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v[c].x, c0));
             w.y = (i + 1 == ih) ? ph : fma(a, v[c].y, c0);
-            *reinterpret_cast<double2 *>(out + i) = w;
+            if (snap_in_bounds(SNAP_SITE_MIXED_ROW, s2 * nx + i + 1, total * nx))
+              *reinterpret_cast<double2 *>(out + i) = w;
           }
         }
       }

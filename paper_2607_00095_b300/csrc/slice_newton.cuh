@@ -25,6 +25,14 @@
 // definite (both of its diagonal values keep >= w_keep of their current value); the
 // second-order condition is checked at the converged point.
 //
+// Stationarity kept along the iteration.  The iteration starts at u = u_hat, lam = 0, where
+// grad_u L = 0, and every trial point is (u(lam_t), lam_t) with lam_t = lam + t dlam and
+// u(lam) = argmin_u L(u, lam): interior u_i = (u_hat_i - dx lam_m) / alpha, boundary
+// u_j = (u_hat_j - dx lam_m) / beta, i.e. a = 1/alpha, c = -dx lam_m / alpha (slice_stationary).
+// With grad_u L = 0 the Newton-KKT step above reduces to S dlam = h.  W stays positive definite
+// (the cap), so L(., lam) is strictly convex and a KKT point reached this way is the unique
+// global minimiser of the slice's projection: the result does not depend on the path.
+//
 // The scalar type T is double (FP64 pipe), float, or df64 (double-float on the FP32 pipe,
 // df64.cuh).  slice_solve_mixed runs the iteration in float while float steps make reliable
 // progress, then continues in df64 to the FP64 stopping tolerance: the same Newton-KKT
@@ -264,6 +272,20 @@ DF_INL df64 sl_cast<df64, float>(float x) { return df64(x, 0.0f); }
 template <>
 DF_INL df64 sl_cast<df64, df64>(df64 x) { return x; }
 
+// u(lam) = argmin_u L(u, lam) in moment form, from z.lm, z.le, z.lb (W positive definite).
+template <class T>
+DF_INL void slice_stationary(const SliceIn<T> &d, SliceZ<T> &z) {
+  const T one = T(1.0f), two = T(2.0f);
+  const T al = one + two * d.dx * z.le;
+  const T be = al + two * z.lb;
+  const T ia = sl_rcp(al), ib = sl_rcp(be);
+  const T dlm = d.dx * z.lm;
+  z.a = ia;
+  z.c = -(dlm * ia);
+  z.p0 = (d.uh0 - dlm) * ib;
+  z.ph = (d.uhh - dlm) * ib;
+}
+
 // Newton-KKT direction at z in precision L: solve S dlam = h - J W^-1 grad L and form
 // du = -W^-1 (grad L + J^T dlam) from the residual components of e.  Returns false when
 // the Schur complement is singular (or cannot be corrected).
@@ -364,9 +386,8 @@ DF_INL void slice_newton_phase(const SliceIn<T> &d, const SliceIn<L> &dl, SliceZ
     SliceZ<T> zt;
     SliceEval<T> et;
     for (;;) {
-      zt.a = z.a + t * dz.a;     zt.c = z.c + t * dz.c;
-      zt.p0 = z.p0 + t * dz.p0;  zt.ph = z.ph + t * dz.ph;
       zt.lm = z.lm + t * dz.lm;  zt.le = z.le + t * dz.le;  zt.lb = z.lb + t * dz.lb;
+      slice_stationary(d, zt);
       slice_eval(d, zt, et);
       if (et.phi <= (T(1) - so.c1x2 * t) * e.phi) { accepted = true; break; }
       if (nb >= so.max_backtracks) break;
@@ -381,7 +402,9 @@ DF_INL void slice_newton_phase(const SliceIn<T> &d, const SliceIn<L> &dl, SliceZ
   }
 }
 
-// The whole iteration in one precision T (FP64 reference path).
+// The whole iteration in one precision T (FP64 reference path), with the polishing step of
+// reading R27 (one more Newton step after the stopping test, kept when ||F||_inf does not
+// increase).
 template <class T>
 DF_INL SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
                                            const SolverOpts &o) {
@@ -389,6 +412,21 @@ DF_INL SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> 
   const SliceOptsT<T> so = slice_opts<T>(o, o.tol_kkt);
   slice_eval(d, z, e);
   slice_newton_phase<T, T>(d, d, z, e, so, so, o.max_iter, R);
+  if (R.status == SNAP_SAMPLE_OK) {
+    SliceZ<T> dz;
+    int corr = 0;
+    if (slice_direction(d, z, e, 0, so.delta0, dz, corr)) {
+      SliceZ<T> zt;
+      zt.lm = z.lm + dz.lm; zt.le = z.le + dz.le; zt.lb = z.lb + dz.lb;
+      slice_stationary(d, zt);
+      SliceEval<T> et;
+      slice_eval(d, zt, et);
+      if (et.res <= e.res && et.alpha > T(0) && et.beta > T(0)) {
+        z = zt;
+        e = et;
+      }
+    }
+  }
   if (R.status == SNAP_SAMPLE_OK && !slice_sosc(d, z, e)) R.status = SNAP_SAMPLE_NOT_MINIMUM;
   return R;
 }
@@ -409,16 +447,180 @@ DF_INL SliceIn<T> slice_in_cast(const SliceIn<S> &s) {
 
 DF_INL df64 df_from_float(float x) { return df64(x, 0.0f); }
 
-// Mixed precision: float steps while they make reliable progress, then steps whose residual
-// F and merit are evaluated in df64 while the Newton system is still solved in float
-// (iterative refinement of the Newton step), to o.tol_kkt.  The float phase stops when ||F||_inf <= max(1e-5 ||F(z0)||_inf, 1e-6 * scale)
-// (scale = the largest magnitude among the slice data; float rounding puts a floor near
-// 1e-7 * scale under ||F||), when a line search needs more than 8 halvings (the float merit
-// is then at its rounding floor), or when only 8 steps of the iteration budget are left.  dd holds the
-// inputs in df64; the result z is returned in df64.
+// Row residuals at the stationary point u(lam) of the current multipliers.  Along the
+// iteration u = u(lam) (slice_stationary), so grad_u L = 0 up to rounding (relative 2^-23 in
+// float, 2^-46 in double-float, both far below the phase tolerances) and F = (0, h): the loop
+// evaluates h and phi = 1/2 ||h||^2 only, and the full ||F||_inf (with grad_u L) is evaluated
+// once at the returned point.
+template <class T>
+struct SliceH {
+  T alpha, beta, su, su2, hm, he, hb;
+  float phi, res;
+};
+
+DF_INL float sl_hi(float x) { return x; }
+DF_INL float sl_hi(df64 x) { return x.hi; }
+
+template <class T>
+DF_INL void slice_eval_h(const SliceIn<T> &d, const SliceZ<T> &z, SliceH<T> &e) {
+  const T one = sl_cast<T, float>(1.0f), two = sl_cast<T, float>(2.0f);
+  const T zero = sl_cast<T, float>(0.0f);
+  e.alpha = one + two * d.dx * z.le;
+  e.beta = e.alpha + two * z.lb;
+  e.su = z.a * d.S1 + z.c * d.n;
+  e.su2 = z.a * z.a * d.S2 + two * z.a * z.c * d.S1 + z.c * z.c * d.n;
+  const T pp = z.p0 * z.p0 + z.ph * z.ph;
+  e.hm = (d.rows & SL_MASS) ? d.dx * (e.su + z.p0 + z.ph) - d.M : zero;
+  e.he = (d.rows & SL_ENERGY) ? d.dx * (e.su2 + pp) - d.E : zero;
+  e.hb = (d.rows & SL_BOUND) ? pp - d.C : zero;
+  const float hm = sl_hi(e.hm), he = sl_hi(e.he), hb = sl_hi(e.hb);
+  e.phi = 0.5f * (hm * hm + he * he + hb * hb);
+  float r = fmaxf(fmaxf(fabsf(hm), fabsf(he)), fabsf(hb));
+  if (e.phi != e.phi) r = e.phi;
+  e.res = r;
+}
+
+// The multiplier step S dlam = h (Appendix B's Newton-KKT step with grad_u L = 0), the
+// Schur complement assembled at the float image of the current point.  False when S is
+// singular.
+DF_INL bool slice_step_h(const SliceIn<float> &d, const SliceZ<float> &z, float alpha,
+                         float beta, float su, float su2, float hm, float he, float hb,
+                         float &dlm, float &dle, float &dlb) {
+  if (alpha == 0.0f || beta == 0.0f) return false;
+  float s00, s01, s02, s11, s12, s22;
+  slice_schur(d, z, su, su2, sl_rcp(alpha), sl_rcp(beta), s00, s01, s02, s11, s12, s22);
+  Ldl3<float> f;
+  if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) return false;
+  ldl3_solve(f, (d.rows & SL_MASS) ? hm : 0.0f, (d.rows & SL_ENERGY) ? he : 0.0f,
+             (d.rows & SL_BOUND) ? hb : 0.0f, dlm, dle, dlb);
+  return true;
+}
+
+// Newton steps in the multipliers from z (evaluated in e) until e.res <= tol, a failure or
+// `budget` steps, with the residuals and trial points in precision T and every step solved in
+// float (T = df64: mixed-precision iterative refinement of the step).  First trial capped so
+// that both diagonal values of W keep >= w_keep of their value, Armijo on phi.
+template <class T>
+DF_INL void slice_newton_h(const SliceIn<T> &d, const SliceIn<float> &d32, SliceZ<T> &z,
+                           SliceH<T> &e, float tol, float c1x2, float w_keep1, bool cap,
+                           int max_backtracks, int budget, SliceResult &R) {
+  for (int it = 0;; ++it) {
+    if (!isfinite(e.res)) { R.status = SNAP_SAMPLE_NONFINITE; return; }
+    if (e.res <= tol) { R.status = SNAP_SAMPLE_OK; return; }
+    if (it >= budget) { R.status = SNAP_SAMPLE_MAXITER; return; }
+    const SliceZ<float> zf{sl_hi(z.a), sl_hi(z.c), sl_hi(z.p0), sl_hi(z.ph),
+                           sl_hi(z.lm), sl_hi(z.le), sl_hi(z.lb)};
+    float dlm, dle, dlb;
+    if (!slice_step_h(d32, zf, sl_hi(e.alpha), sl_hi(e.beta), sl_hi(e.su), sl_hi(e.su2),
+                      sl_hi(e.hm), sl_hi(e.he), sl_hi(e.hb), dlm, dle, dlb)) {
+      R.status = SNAP_SAMPLE_SINGULAR;
+      return;
+    }
+    float t = 1.0f;
+    if (cap) {
+      const float da = 2.0f * d32.dx * dle, db = da + 2.0f * dlb;
+      const float al = sl_hi(e.alpha), be = sl_hi(e.beta);
+      if (al > 0.0f && da < 0.0f) t = fminf(t, w_keep1 * al * df_rcp(-da));
+      if (be > 0.0f && db < 0.0f) t = fminf(t, w_keep1 * be * df_rcp(-db));
+    }
+    int nb = 0;
+    bool accepted = false;
+    SliceZ<T> zt;
+    SliceH<T> et;
+    for (;;) {
+      const T tt = sl_cast<T, float>(t);
+      zt.lm = z.lm + tt * sl_cast<T, float>(dlm);
+      zt.le = z.le + tt * sl_cast<T, float>(dle);
+      zt.lb = z.lb + tt * sl_cast<T, float>(dlb);
+      slice_stationary(d, zt);
+      slice_eval_h(d, zt, et);
+      if (et.phi <= (1.0f - c1x2 * t) * e.phi) { accepted = true; break; }
+      if (nb >= max_backtracks) break;
+      nb++;
+      t *= 0.5f;
+    }
+    R.backtracks += nb;
+    if (!accepted) { R.status = SNAP_SAMPLE_LINESEARCH; return; }
+    z = zt;
+    e = et;
+    R.iters++;
+  }
+}
+
+// Polishing step after the stopping test (reading R27): the test bounds ||h||, and the
+// multipliers only through the conditioning of S, which is large on slices whose boundary
+// circle is nearly degenerate (c_k ~ 1e-6: S ~ 1e7 there).  One more Newton step with the
+// Schur system assembled and solved in double-float (not float) leaves the multipliers at
+// the rounding level; it is kept when it does not increase ||h||_inf.
+DF_INL void slice_polish_df64(const SliceIn<df64> &d, SliceZ<df64> &z, SliceH<df64> &e,
+                              SliceResult &R) {
+  const df64 zero(0.0f, 0.0f), one(1.0f, 0.0f);
+  if (!(e.alpha > zero) || !(e.beta > zero)) return;
+  df64 s00, s01, s02, s11, s12, s22;
+  slice_schur(d, z, e.su, e.su2, one / e.alpha, one / e.beta, s00, s01, s02, s11, s12, s22);
+  Ldl3<df64> f;
+  if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) return;
+  df64 dlm, dle, dlb;
+  ldl3_solve(f, (d.rows & SL_MASS) ? e.hm : zero, (d.rows & SL_ENERGY) ? e.he : zero,
+             (d.rows & SL_BOUND) ? e.hb : zero, dlm, dle, dlb);
+  SliceZ<df64> zt;
+  zt.lm = z.lm + dlm;
+  zt.le = z.le + dle;
+  zt.lb = z.lb + dlb;
+  slice_stationary(d, zt);
+  SliceH<df64> et;
+  slice_eval_h(d, zt, et);
+  if (et.res <= e.res && et.alpha > zero && et.beta > zero) {
+    z = zt;
+    e = et;
+  }
+}
+
+// Start of the multiplier iteration inside the region W > 0, where the KKT point is unique
+// (so the start changes the path, not the result): with mass and energy rows, the
+// multipliers of the slice projection without the boundary row (hyperplane and sphere:
+// u = M + rho w / ||w|| over all nx points, alpha = ||w|| / rho, lam_m = (mean - alpha M) / dx
+// in the per-point scaling), and with the boundary row the lam_b that puts the two boundary
+// values on the circle u_0^2 + u_h^2 = C at that lam_m (beta = |u_hat_b - dx lam_m| / sqrt(C)).
+// Left at lam = 0 (u = u_hat) when any of these is not finite or leaves W positive definite.
+DF_INL void slice_warm_start(const SliceIn<float> &d, SliceZ<float> &z) {
+  if ((d.rows & (SL_MASS | SL_ENERGY)) != (SL_MASS | SL_ENERGY)) return;
+  const float N = d.n + 2.0f;
+  const float s1 = d.S1 + d.uh0 + d.uhh;
+  const float s2 = d.S2 + d.uh0 * d.uh0 + d.uhh * d.uhh;
+  const float mean = s1 / N;
+  const float w2 = s2 - N * mean * mean;
+  const float mbar = d.M / (N * d.dx);
+  const float rho2 = d.E / d.dx - N * mbar * mbar;
+  if (!(w2 > 0.0f && rho2 > 0.0f)) return;
+  const float al = sqrtf(w2 / rho2);
+  const float lm = (mean - al * mbar) / d.dx;
+  const float le = (al - 1.0f) / (2.0f * d.dx);
+  float lb = 0.0f;
+  if ((d.rows & SL_BOUND) && d.C > 0.0f) {
+    const float v0 = d.uh0 - d.dx * lm, vh = d.uhh - d.dx * lm;
+    const float be = sqrtf((v0 * v0 + vh * vh) / d.C);
+    if (be > 1e-3f * al && be < 1e30f) lb = 0.5f * (be - al);
+  }
+  if (!(al > 0.0f && isfinite(lm) && isfinite(le) && isfinite(lb))) return;
+  z.lm = lm;
+  z.le = le;
+  z.lb = lb;
+  slice_stationary(d, z);
+}
+
+// Mixed precision: float steps while they make reliable progress, then steps whose residuals
+// and merit are evaluated in df64 while the step is still solved in float (iterative
+// refinement of the Newton step), to o.tol_kkt.  The float phase stops when
+// ||h||_inf <= max(1e-5 ||h(z0)||_inf, 1e-6 * scale) (scale = the largest magnitude among
+// the slice data; float rounding puts a floor near 1e-7 * scale under ||h||), when a line
+// search needs more than 8 halvings (the float merit is then at its rounding floor), or when
+// only 8 steps of the iteration budget are left.  dd holds the inputs in df64; the result z is
+// returned in df64 and e is the full evaluation (grad_u L included) at it.
 DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
                                      SliceEval<df64> &e, const SolverOpts &o,
                                      const SliceOptsT<float> &sf, const SliceOptsT<df64> &sd) {
+  (void)sd;
   SliceResult R{0, 0, SNAP_SAMPLE_OK, 0};
   SliceIn<float> d32;
   d32.S1 = dd.S1.hi; d32.S2 = dd.S2.hi; d32.mx = dd.mx.hi; d32.mn = dd.mn.hi;
@@ -426,29 +628,34 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
   d32.M = dd.M.hi; d32.E = dd.E.hi; d32.C = dd.C.hi;
   d32.rows = dd.rows;
   d32.nint = dd.nint;
+  const float c1x2 = sf.c1x2, wk1 = sf.w_keep1;
   SliceZ<float> z32{z.a.hi, z.c.hi, z.p0.hi, z.ph.hi, z.lm.hi, z.le.hi, z.lb.hi};
-  SliceEval<float> e32;
-  slice_eval(d32, z32, e32);
-  if (sl_finite(e32.res)) {
-    SliceOptsT<float> s32 = sf;
-    s32.max_backtracks = o.max_backtracks < 8 ? o.max_backtracks : 8;
+  slice_warm_start(d32, z32);
+  SliceH<float> e32;
+  slice_eval_h(d32, z32, e32);
+  if (isfinite(e32.res)) {
     float scale = fmaxf(fmaxf(fabsf(d32.mx), fabsf(d32.mn)), fmaxf(fabsf(d32.uh0), fabsf(d32.uhh)));
     scale = fmaxf(scale, fmaxf(fabsf(d32.M), sqrtf(fabsf(d32.E) + fabsf(d32.C))));
-    float tol32 = fmaxf(1e-5f * e32.res, 1e-6f * scale);
-    if (tol32 > s32.tol) s32.tol = tol32;
+    const float tol32 = fmaxf(fmaxf(1e-5f * e32.res, 1e-6f * scale), sf.tol);
     const int budget32 = o.max_iter > 16 ? o.max_iter - 8 : o.max_iter / 2;
-    slice_newton_phase<float, float>(d32, d32, z32, e32, s32, s32, budget32, R);
+    slice_newton_h<float>(d32, d32, z32, e32, tol32, c1x2, wk1, sf.cap,
+                          o.max_backtracks < 8 ? o.max_backtracks : 8, budget32, R);
     if (R.status != SNAP_SAMPLE_NONFINITE) {
-      z.a = df_from_float(z32.a); z.c = df_from_float(z32.c);
-      z.p0 = df_from_float(z32.p0); z.ph = df_from_float(z32.ph);
       z.lm = df_from_float(z32.lm); z.le = df_from_float(z32.le); z.lb = df_from_float(z32.lb);
     }
   }
   R.status = SNAP_SAMPLE_OK;
+  slice_stationary(dd, z);
+  SliceH<df64> eh;
+  slice_eval_h(dd, z, eh);
+  slice_newton_h<df64>(dd, d32, z, eh, sf.tol, c1x2, wk1, sf.cap, o.max_backtracks,
+                       o.max_iter - R.iters, R);
+  if (R.status == SNAP_SAMPLE_OK) slice_polish_df64(dd, z, eh, R);
+  // the full residual (grad_u L included) at the returned point
   slice_eval(dd, z, e);
-  slice_newton_phase<df64, float>(dd, d32, z, e, sd, sf, o.max_iter - R.iters, R);
-  if (R.status == SNAP_SAMPLE_OK) {
-    // second-order check on the float image of the converged point (a sign test)
+  if (R.status == SNAP_SAMPLE_OK && !(e.res <= sd.tol)) R.status = SNAP_SAMPLE_MAXITER;
+  if (R.status == SNAP_SAMPLE_OK && !(e.alpha > df64(0.0f, 0.0f) && e.beta > df64(0.0f, 0.0f))) {
+    // W not positive definite: second-order check by the inertia of K
     SliceZ<float> zf{z.a.hi, z.c.hi, z.p0.hi, z.ph.hi, z.lm.hi, z.le.hi, z.lb.hi};
     SliceEval<float> ef;
     slice_eval(d32, zf, ef);

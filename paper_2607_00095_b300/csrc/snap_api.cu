@@ -6,6 +6,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "kern_1dflux.h"
@@ -166,6 +167,46 @@ void build_pattern_flux(snap_problem *p, int nx, int nt, int K) {
   p->info.n_rows_active = na;
 }
 
+// Family F (heat): IC rows, mass rows (implied), Crank-Nicolson rows k = 1..nt-1 (three
+// stencil columns in slices k-1 and k), energy rows (implied; every column of slices k-1, k).
+void build_pattern_heat(snap_problem *p, int nx, int nt) {
+  std::vector<int> rp(1, 0), ci;
+  std::vector<unsigned char> act;
+  for (int i = 0; i < nx; ++i) { ci.push_back(i); rp.push_back((int)ci.size()); act.push_back(1); }
+  for (int k = 0; k < nt; ++k) {
+    for (int i = 0; i < nx; ++i) ci.push_back(k * nx + i);
+    rp.push_back((int)ci.size());
+    act.push_back(0);
+  }
+  for (int k = 1; k < nt; ++k)
+    for (int i = 0; i < nx; ++i) {
+      std::vector<int> c;
+      for (int kk = k - 1; kk <= k; ++kk)
+        for (int d = -1; d <= 1; ++d) c.push_back(kk * nx + (i + d + nx) % nx);
+      std::sort(c.begin(), c.end());
+      c.erase(std::unique(c.begin(), c.end()), c.end());
+      ci.insert(ci.end(), c.begin(), c.end());
+      rp.push_back((int)ci.size());
+      act.push_back(1);
+    }
+  for (int k = 1; k < nt; ++k) {
+    for (int i = 0; i < 2 * nx; ++i) ci.push_back((k - 1) * nx + i);
+    rp.push_back((int)ci.size());
+    act.push_back(0);
+  }
+  const int m = (int)rp.size() - 1;
+  p->row_ptr = (int *)malloc(sizeof(int) * rp.size());
+  p->col_idx = (int *)malloc(sizeof(int) * (ci.size() + 1));
+  p->active = (unsigned char *)malloc(m + 1);
+  memcpy(p->row_ptr, rp.data(), sizeof(int) * rp.size());
+  memcpy(p->col_idx, ci.data(), sizeof(int) * ci.size());
+  memcpy(p->active, act.data(), m);
+  int na = 0;
+  for (unsigned char a : act) na += a;
+  p->info.pattern_nnz = (long long)ci.size();
+  p->info.n_rows_active = na;
+}
+
 // 2-D family C: divergence rows [f][j][i] (4 stencil columns), then one energy row per frame.
 void build_pattern_2d(snap_problem *p, int N, int nt) {
   std::vector<int> rp(1, 0), ci;
@@ -212,6 +253,7 @@ snap_status check_batch(const snap_problem *p, int B) {
 }
 
 size_t ws_bytes(const snap_problem *p, int B) {
+  if (p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY) return 0;
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) return ws_bytes_2d(p, B);
   if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) return ws_bytes_1dbc(p, B);
   if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) return ws_bytes_1dflux(p, B);
@@ -233,6 +275,29 @@ snap_status snap_check_options(const snap_options &o) { return check_opts(o); }
 extern "C" {
 
 const char *snap_last_error(void) { return g_err; }
+
+#ifdef SNAP_BOUNDS_CHECK
+}  // extern "C"
+__device__ unsigned long long g_snap_bounds_err = 0ull;
+extern "C" {
+snap_status snap_bounds_error(unsigned long long *word, int clear) {
+  if (!word) return fail(SNAP_ERR_INVALID_ARG, "null output");
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_snap_bounds_err, sizeof(unsigned long long));
+  if (e != cudaSuccess) return cuda_fail(e, "reading the bounds error word");
+  if (clear) {
+    const unsigned long long zero = 0ull;
+    e = cudaMemcpyToSymbol(g_snap_bounds_err, &zero, sizeof(zero));
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the bounds error word");
+  }
+  return SNAP_OK;
+}
+#else
+snap_status snap_bounds_error(unsigned long long *word, int clear) {
+  (void)clear;
+  if (word) *word = 0ull;
+  return fail(SNAP_ERR_UNSUPPORTED, "this library was built without SNAP_BOUNDS_CHECK");
+}
+#endif
 
 const char *snap_version(void) { return SNAP_VERSION_STRING; }
 
@@ -358,6 +423,18 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
       build_pattern_flux(p, d->nx, d->nt, d->n_flux);
       break;
     }
+    case SNAP_FAMILY_F_HEAT_ENERGY: {
+      if (d->nx < 3 || d->nx > 512 || d->nt < 2 || d->rows != 0) {
+        free(p);
+        return fail(SNAP_ERR_INVALID_ARG, "family F: nx in [3, 512], nt >= 2, rows 0");
+      }
+      p->info.n_vars = d->nx * d->nt;
+      p->info.n_rows_nominal = d->nx + d->nt + (d->nt - 1) * d->nx + (d->nt - 1);
+      p->info.n_params = d->nx + 1;
+      p->info.n_blocks = 1;
+      build_pattern_heat(p, d->nx, d->nt);
+      break;
+    }
     case SNAP_FAMILY_TOY_LEFT_RIEMANN: {
       if (d->nx < 2 || d->nx > 4096) {
         free(p);
@@ -421,7 +498,8 @@ snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes) {
   if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) *bytes = cache_bytes_2d(p, B);
   else if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN ||
            p->desc.family == SNAP_FAMILY_D_BURGERS_BC ||
-           p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX) *bytes = 0;
+           p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX ||
+           p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY) *bytes = 0;
   else *bytes = sizeof(SliceFactor) * (size_t)B * p->g1.nt;
   return SNAP_OK;
 }
@@ -448,7 +526,7 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
   if (u == u_hat || u == u0 || (double *)lambda == u)
     return fail(SNAP_ERR_INVALID_ARG, "outputs may not alias inputs");
   const size_t need = ws_bytes(p, B);
-  if (!workspace || workspace_bytes < need)
+  if (need > 0 && (!workspace || workspace_bytes < need))
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   int path = o.path;
   if ((path == SNAP_PATH_MOMENT || path == SNAP_PATH_MIXED) && u0 && u0 != u_hat)
@@ -457,7 +535,10 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
   if (u0 == u_hat) u0 = nullptr;
   const SolverOpts so = to_solver(o);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) {
+  if (p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY) {
+    if (u0) return fail(SNAP_ERR_UNSUPPORTED, "family F starts at u_hat (square active rows)");
+    e = launch_heat_forward(p, B, u_hat, params, u, lambda, stats, o.tol_h, (cudaStream_t)stream);
+  } else if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC) {
     if (u0) return fail(SNAP_ERR_UNSUPPORTED, "family D starts at u_hat (linear rows: one step)");
     e = launch_1dbc_forward(p, B, u_hat, params, u, lambda, stats, so, workspace,
                             (cudaStream_t)stream);
@@ -493,10 +574,13 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
   if (!aligned16(grad_u) || !aligned16(u) || !aligned16(grad_u_hat))
     return fail(SNAP_ERR_INVALID_ARG, "grad_u, u and grad_u_hat must be 16-byte aligned");
   const size_t need = ws_bytes(p, B);
-  if (!workspace || workspace_bytes < need)
+  if (need > 0 && (!workspace || workspace_bytes < need))
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
+  if (p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY)
+    e = launch_heat_backward(p, B, grad_u, u, params, stats, grad_u_hat, grad_params,
+                             (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
     e = launch_1dbc_backward(p, B, grad_u, stats, grad_u_hat, grad_params, workspace,
                              (cudaStream_t)stream);
   else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
@@ -525,10 +609,12 @@ snap_status snap_constraint_residual(snap_problem_t p, int B, const double *u,
   if (B == 0) return SNAP_OK;
   if (!u || !params) return fail(SNAP_ERR_INVALID_ARG, "null u / params");
   const size_t need = ws_bytes(p, B);
-  if (!workspace || workspace_bytes < need)
+  if (need > 0 && (!workspace || workspace_bytes < need))
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);
   cudaError_t e;
-  if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
+  if (p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY)
+    e = launch_heat_residual(p, B, u, params, h, h_inf, (cudaStream_t)stream);
+  else if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
     e = launch_1dbc_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);
   else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
     e = launch_1dflux_residual(p, B, u, params, h, h_inf, workspace, (cudaStream_t)stream);

@@ -19,7 +19,8 @@ __host__ __device__ inline int snap_status_rank(int s) {
     case SNAP_SAMPLE_NOT_MINIMUM: return 5;
     case SNAP_SAMPLE_SINGULAR: return 6;
     case SNAP_SAMPLE_NONFINITE: return 7;
-    default: return 8;
+    case SNAP_SAMPLE_DEVICE_WAIT: return 8;
+    default: return 9;
   }
 }
 
@@ -154,6 +155,16 @@ cudaError_t launch_1dbc_backward(const snap_problem *p, int B, const double *gra
 cudaError_t launch_1dbc_residual(const snap_problem *p, int B, const double *u,
                                  const double *params, double *h, double *h_inf, void *ws,
                                  cudaStream_t s);
+
+// Family F (kern_heat.cu).
+cudaError_t launch_heat_forward(const snap_problem *p, int B, const double *u_hat,
+                                const double *params, double *u, double *lambda,
+                                snap_stats *stats, double tol_h, cudaStream_t s);
+cudaError_t launch_heat_residual(const snap_problem *p, int B, const double *u,
+                                 const double *params, double *h, double *h_inf, cudaStream_t s);
+cudaError_t launch_heat_backward(const snap_problem *p, int B, const double *grad_u,
+                                 const double *u, const double *params, const snap_stats *stats,
+                                 double *grad_u_hat, double *grad_params, cudaStream_t s);
 
 // Alignment helper for workspace carving.
 inline size_t snap_align256(size_t x) { return (x + 255) & ~(size_t)255; }

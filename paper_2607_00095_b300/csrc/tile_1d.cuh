@@ -60,6 +60,162 @@ __device__ __forceinline__ df64 t1_shfl_df(df64 v, int off) {
   return df64(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
 }
 
+// Phase 2 for one slice k >= 1 (one lane): the slice's Newton-KKT iteration from its interior
+// moments (m1, m2: S1, S2 in double-float; mmx, mmn: interior extremes; mok: every value in
+// the float-pair range), u_hat at i = 0 and i = nx/2 (uh0, uhh) and the sample's derived
+// values; writes the slice's multipliers into lb, its statistics into *stat and, when cf is
+// not null, its adjoint factor.  Returns u = A u_hat + Cc on the interior, P0 / PH at i = 0 /
+// nx/2.  row (u_hat of the slice, any address space) is read only by the FP64 fallback.
+__device__ __forceinline__ void t1_solve_slice(
+    const Geom1D &g, int k, const df64 &m1, const df64 &m2, float mmx, float mmn, int mok,
+    double uh0, double uhh, const double *row, const double *__restrict__ pg,
+    const SampleDerived &dv, double *__restrict__ lb, BlockStat *__restrict__ stat,
+    SliceFactor *__restrict__ cf, const SolverOpts &o, const SliceOptsT<float> &so_f,
+    const SliceOptsT<df64> &so_d, const df64 &dxd, double &A, double &Cc, double &P0,
+    double &PH) {
+  const int nx = g.nx, ih = g.ih;
+  BlockStat st;
+  const double C = (g.rows & SL_BOUND) ? __ldg(pg + g.p_c + k) : 0.0;
+  double hm, he, hb, res, S1d, S2d;
+  SliceResult R;
+  double lmd, led, lbd;
+  float u0h, u0l, uhh_h, uhh_l, ch, cl;
+  const bool range_ok = mok && df_split(uh0, u0h, u0l) && df_split(uhh, uhh_h, uhh_l) &&
+                        df_split(C, ch, cl);
+  if (range_ok) {
+    SliceIn<df64> d;
+    d.S1 = m1; d.S2 = m2;
+    d.mx = df64(mmx, 0.0f); d.mn = df64(mmn, 0.0f);
+    d.uh0 = df64(u0h, u0l); d.uhh = df64(uhh_h, uhh_l);
+    d.n = df64((float)(nx - 2), 0.0f);
+    d.nint = nx - 2;
+    d.dx = dxd;
+    d.M = df64(dv.Mh, dv.Ml);
+    df64 E(0.0f, 0.0f);
+    if (g.rows & SL_ENERGY) {
+      const df64 e = df64(dv.E0h, dv.E0l) * t1_df_pow(df64(dv.qh, dv.ql), k);
+      const df64 fl = df64(dv.fh, dv.fl);
+      E = (e >= fl) ? e : fl;
+    }
+    d.E = E;
+    d.C = df64(ch, cl);
+    d.rows = g.rows;
+    const df64 zero(0.0f, 0.0f);
+    const bool infeasible = ((g.rows & SL_BOUND) && ch < 0.0f) ||
+                            ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? d.M * d.M : zero));
+    SliceZ<df64> z{df64(1.0f, 0.0f), zero, d.uh0, d.uhh, zero, zero, zero};
+    SliceEval<df64> e;
+    if (infeasible) {
+      slice_eval(d, z, e);
+      R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
+    } else {
+      R = slice_solve_mixed(d, z, e, o, so_f, so_d);
+    }
+    A = (double)z.a; Cc = (double)z.c; P0 = (double)z.p0; PH = (double)z.ph;
+    lmd = (double)z.lm; led = (double)z.le; lbd = (double)z.lb;
+    // statistics in double-float, one conversion each
+    const df64 hmx = sl_max(sl_max(sl_abs(e.hm), sl_abs(e.he)), sl_abs(e.hb));
+    const df64 am1 = z.a - df64(1.0f, 0.0f);
+    const df64 d0 = z.p0 - d.uh0, dh = z.ph - d.uhh;
+    const df64 obj = (am1 * am1 * d.S2 + df64(2.0f, 0.0f) * am1 * z.c * d.S1 + z.c * z.c * d.n +
+                      d0 * d0 + dh * dh) * df64(0.5f, 0.0f);
+    st.iters = R.iters;
+    st.backtracks = R.backtracks;
+    st.status = R.status;
+    st.corrections = R.corrections;
+    st.kkt_inf = (double)e.res;
+    st.h_inf = (double)hmx;
+    st.obj = (double)obj;
+    if (e.res != e.res) st.kkt_inf = NAN;
+    if (hmx != hmx) st.h_inf = NAN;
+    if (cf) {
+      const double al = (double)e.alpha, be = (double)e.beta;
+      S1d = (double)m1; S2d = (double)m2;
+      SliceIn<double> d64 = slice_in_cast<double>(d);
+      SliceZ<double> z64{A, Cc, P0, PH, lmd, led, lbd};
+      double s00, s01, s02, s11, s12, s22;
+      slice_schur(d64, z64, A * S1d + Cc * (double)(nx - 2),
+                  A * A * S2d + 2.0 * A * Cc * S1d + Cc * Cc * (double)(nx - 2), 1.0 / al,
+                  1.0 / be, s00, s01, s02, s11, s12, s22);
+      Ldl3<double> f;
+      if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
+        f.d0 = f.d1 = f.d2 = 0.0;
+        f.l10 = f.l20 = f.l21 = 0.0;
+      }
+      SliceFactor sf{al, be, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
+      *cf = sf;
+    }
+  } else {
+    // FP64 fallback: moments in FP64 by this lane, FP64 iteration
+    double a1 = 0.0, a2 = 0.0, mx = -INFINITY, mn = INFINITY;
+    for (int i = 0; i < nx; ++i) {
+      if (i == 0 || i == ih) continue;
+      const double v = row[i];
+      a1 += v;
+      a2 = fma(v, v, a2);
+      mx = fmax(mx, v);
+      mn = fmin(mn, v);
+      if (v != v) mx = v;
+    }
+    SliceIn<double> d;
+    d.S1 = a1; d.S2 = a2; d.mx = mx; d.mn = mn;
+    d.uh0 = uh0; d.uhh = uhh;
+    d.n = (double)(nx - 2);
+    d.nint = nx - 2;
+    d.dx = g.dx;
+    d.M = dv.M;
+    double E = 0.0;
+    if (g.rows & SL_ENERGY) {
+      const double e = dv.E0 * exp(-__ldg(pg + g.p_rate) * ((double)k / (double)(g.nt - 1)));
+      const double fl = dv.M * dv.M + g.energy_floor;
+      E = e >= fl ? e : fl;
+    }
+    d.E = E;
+    d.C = C;
+    d.rows = g.rows;
+    const bool infeasible = ((g.rows & SL_BOUND) && C < 0.0) ||
+                            ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? dv.M * dv.M : 0.0));
+    SliceZ<double> z{1.0, 0.0, uh0, uhh, 0.0, 0.0, 0.0};
+    SliceEval<double> e;
+    if (infeasible) {
+      slice_eval(d, z, e);
+      R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
+    } else {
+      R = slice_newton(d, z, e, o);
+    }
+    A = z.a; Cc = z.c; P0 = z.p0; PH = z.ph;
+    lmd = z.lm; led = z.le; lbd = z.lb;
+    hm = e.hm; he = e.he; hb = e.hb; res = e.res;
+    S1d = a1; S2d = a2;
+    if (cf) {
+      double s00, s01, s02, s11, s12, s22;
+      slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
+      Ldl3<double> f;
+      if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
+        f.d0 = f.d1 = f.d2 = 0.0;
+        f.l10 = f.l20 = f.l21 = 0.0;
+      }
+      SliceFactor sf{e.alpha, e.beta, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
+      *cf = sf;
+    }
+  }
+  if (!range_ok) {
+    st.iters = R.iters;
+    st.backtracks = R.backtracks;
+    st.status = R.status;
+    st.corrections = R.corrections;
+    st.kkt_inf = res;
+    st.h_inf = t1_nan_max(t1_nan_max(fabs(hm), fabs(he)), fabs(hb));
+    const double am1 = A - 1.0;
+    st.obj = 0.5 * (am1 * am1 * S2d + 2.0 * am1 * Cc * S1d + Cc * Cc * (double)(nx - 2) +
+                    (P0 - uh0) * (P0 - uh0) + (PH - uhh) * (PH - uhh));
+  }
+  if (g.off_mass >= 0) lb[g.off_mass + k] = lmd;
+  if (g.off_energy >= 0) lb[g.off_energy + k] = led;
+  if (g.off_bound >= 0) lb[g.off_bound + k] = lbd;
+  *stat = st;
+}
+
 template <class Addr>
 __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long long sbase,
                                            long long send, const SolverOpts &o,
@@ -155,157 +311,12 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
   double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
   if (s < send) {
     const int k = ad.slice_k(s);
-    const double *pg = ad.par(s);
-    double *lb = ad.lam_of(s);
-    const double *row = ad.row_in(s);
-    const SampleDerived dv = ad.derived(s);
-    BlockStat st;
-    if (k == 0) {
-      // IC slice: written by the prepare kernel
-    } else {
+    if (k != 0) {     // IC slice (k = 0): solved by the caller
+      const double *row = ad.row_in(s);
       kind = T1_KIND_MOMENT;
-      const double uh0 = __ldg(row), uhh = __ldg(row + ih);
-      const double C = (g.rows & SL_BOUND) ? __ldg(pg + g.p_c + k) : 0.0;
-      double hm, he, hb, res, S1d, S2d;
-      SliceResult R;
-      double lmd, led, lbd;
-      float u0h, u0l, uhh_h, uhh_l, ch, cl;
-      const bool range_ok = mok && df_split(uh0, u0h, u0l) && df_split(uhh, uhh_h, uhh_l) &&
-                            df_split(C, ch, cl);
-      if (range_ok) {
-        SliceIn<df64> d;
-        d.S1 = m1; d.S2 = m2;
-        d.mx = df64(mmx, 0.0f); d.mn = df64(mmn, 0.0f);
-        d.uh0 = df64(u0h, u0l); d.uhh = df64(uhh_h, uhh_l);
-        d.n = df64((float)(nx - 2), 0.0f);
-        d.nint = nx - 2;
-        d.dx = dxd;
-        d.M = df64(dv.Mh, dv.Ml);
-        df64 E(0.0f, 0.0f);
-        if (g.rows & SL_ENERGY) {
-          const df64 e = df64(dv.E0h, dv.E0l) * t1_df_pow(df64(dv.qh, dv.ql), k);
-          const df64 fl = df64(dv.fh, dv.fl);
-          E = (e >= fl) ? e : fl;
-        }
-        d.E = E;
-        d.C = df64(ch, cl);
-        d.rows = g.rows;
-        const df64 zero(0.0f, 0.0f);
-        const bool infeasible = ((g.rows & SL_BOUND) && ch < 0.0f) ||
-                                ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? d.M * d.M : zero));
-        SliceZ<df64> z{df64(1.0f, 0.0f), zero, d.uh0, d.uhh, zero, zero, zero};
-        SliceEval<df64> e;
-        if (infeasible) {
-          slice_eval(d, z, e);
-          R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
-        } else {
-          R = slice_solve_mixed(d, z, e, o, so_f, so_d);
-        }
-        A = (double)z.a; Cc = (double)z.c; P0 = (double)z.p0; PH = (double)z.ph;
-        lmd = (double)z.lm; led = (double)z.le; lbd = (double)z.lb;
-        // statistics in double-float, one conversion each
-        const df64 hmx = sl_max(sl_max(sl_abs(e.hm), sl_abs(e.he)), sl_abs(e.hb));
-        const df64 am1 = z.a - df64(1.0f, 0.0f);
-        const df64 d0 = z.p0 - d.uh0, dh = z.ph - d.uhh;
-        const df64 obj = (am1 * am1 * d.S2 + df64(2.0f, 0.0f) * am1 * z.c * d.S1 + z.c * z.c * d.n +
-                          d0 * d0 + dh * dh) * df64(0.5f, 0.0f);
-        st.iters = R.iters;
-        st.backtracks = R.backtracks;
-        st.status = R.status;
-        st.corrections = R.corrections;
-        st.kkt_inf = (double)e.res;
-        st.h_inf = (double)hmx;
-        st.obj = (double)obj;
-        if (e.res != e.res) st.kkt_inf = NAN;
-        if (hmx != hmx) st.h_inf = NAN;
-        SliceFactor *cf = ad.factor(s);
-        if (cf) {
-          const double al = (double)e.alpha, be = (double)e.beta;
-          S1d = (double)m1; S2d = (double)m2;
-          SliceIn<double> d64 = slice_in_cast<double>(d);
-          SliceZ<double> z64{A, Cc, P0, PH, lmd, led, lbd};
-          double s00, s01, s02, s11, s12, s22;
-          slice_schur(d64, z64, A * S1d + Cc * (double)(nx - 2),
-                      A * A * S2d + 2.0 * A * Cc * S1d + Cc * Cc * (double)(nx - 2), 1.0 / al,
-                      1.0 / be, s00, s01, s02, s11, s12, s22);
-          Ldl3<double> f;
-          if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-            f.d0 = f.d1 = f.d2 = 0.0;
-            f.l10 = f.l20 = f.l21 = 0.0;
-          }
-          SliceFactor sf{al, be, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-          *cf = sf;
-        }
-      } else {
-        // FP64 fallback: moments in FP64 by this lane, FP64 iteration
-        double a1 = 0.0, a2 = 0.0, mx = -INFINITY, mn = INFINITY;
-        for (int i = 0; i < nx; ++i) {
-          if (i == 0 || i == ih) continue;
-          const double v = __ldg(row + i);
-          a1 += v;
-          a2 = fma(v, v, a2);
-          mx = fmax(mx, v);
-          mn = fmin(mn, v);
-          if (v != v) mx = v;
-        }
-        SliceIn<double> d;
-        d.S1 = a1; d.S2 = a2; d.mx = mx; d.mn = mn;
-        d.uh0 = uh0; d.uhh = uhh;
-        d.n = (double)(nx - 2);
-        d.nint = nx - 2;
-        d.dx = g.dx;
-        d.M = dv.M;
-        double E = 0.0;
-        if (g.rows & SL_ENERGY) {
-          const double e = dv.E0 * exp(-__ldg(pg + g.p_rate) * ((double)k / (double)(g.nt - 1)));
-          const double fl = dv.M * dv.M + g.energy_floor;
-          E = e >= fl ? e : fl;
-        }
-        d.E = E;
-        d.C = C;
-        d.rows = g.rows;
-        const bool infeasible = ((g.rows & SL_BOUND) && C < 0.0) ||
-                                ((g.rows & SL_ENERGY) && E < ((g.rows & SL_MASS) ? dv.M * dv.M : 0.0));
-        SliceZ<double> z{1.0, 0.0, uh0, uhh, 0.0, 0.0, 0.0};
-        SliceEval<double> e;
-        if (infeasible) {
-          slice_eval(d, z, e);
-          R = SliceResult{0, 0, SNAP_SAMPLE_INFEASIBLE_PARAMS, 0};
-        } else {
-          R = slice_newton(d, z, e, o);
-        }
-        A = z.a; Cc = z.c; P0 = z.p0; PH = z.ph;
-        lmd = z.lm; led = z.le; lbd = z.lb;
-        hm = e.hm; he = e.he; hb = e.hb; res = e.res;
-        S1d = a1; S2d = a2;
-        SliceFactor *cf = ad.factor(s);
-        if (cf) {
-          double s00, s01, s02, s11, s12, s22;
-          slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
-          Ldl3<double> f;
-          if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-            f.d0 = f.d1 = f.d2 = 0.0;
-            f.l10 = f.l20 = f.l21 = 0.0;
-          }
-          SliceFactor sf{e.alpha, e.beta, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-          *cf = sf;
-        }
-      }
-      if (!range_ok) {
-        st.iters = R.iters;
-        st.backtracks = R.backtracks;
-        st.status = R.status;
-        st.corrections = R.corrections;
-        st.kkt_inf = res;
-        st.h_inf = t1_nan_max(t1_nan_max(fabs(hm), fabs(he)), fabs(hb));
-        const double am1 = A - 1.0;
-        st.obj = 0.5 * (am1 * am1 * S2d + 2.0 * am1 * Cc * S1d + Cc * Cc * (double)(nx - 2) +
-                        (P0 - uh0) * (P0 - uh0) + (PH - uhh) * (PH - uhh));
-      }
-      if (g.off_mass >= 0) lb[g.off_mass + k] = lmd;
-      if (g.off_energy >= 0) lb[g.off_energy + k] = led;
-      if (g.off_bound >= 0) lb[g.off_bound + k] = lbd;
-      *ad.stat(s) = st;
+      t1_solve_slice(g, k, m1, m2, mmx, mmn, mok, __ldg(row), __ldg(row + g.ih), row,
+                     ad.par(s), ad.derived(s), ad.lam_of(s), ad.stat(s), ad.factor(s), o, so_f,
+                     so_d, dxd, A, Cc, P0, PH);
     }
   }
   // ---------------- phase 3: write-back, 4 lanes per slice ----------------

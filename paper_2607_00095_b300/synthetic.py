@@ -19,6 +19,9 @@ Workloads (name -> sizes):
               u0 and perturbation xi ~ N(0, 1) (seed 1006), 10 steps, sigma0 = 0.3
   vorticity_2d  2-D vorticity (IC, total vorticity, enstrophy), B=512, 16x16, nt=50, seed 1007
   burgers_bc_1d  family D (Dirichlet, mass, Neumann per slice), B=512, nx=nt=101, seed 1008
+  burgers_flux_1d  family E (IC, mass, Godunov flux rows), B=512, nx=nt=101, Flux(5), seed 1009
+  heat2_1d    family F (IC, mass, Crank-Nicolson PDE residual, energy evolution), B=512,
+              nx=nt=100 (the heat problem's grid), seed 1010
 """
 import numpy as np
 
@@ -170,6 +173,24 @@ def gen_burgers_flux(seed, B, nx, nt, noise=0.1, eps=0.02):
     return np.ascontiguousarray(u_hat), np.ascontiguousarray(g)
 
 
+def gen_heat(seed, B, nx, nt, noise=0.1):
+    """Heat problem on the periodic [0, 2 pi) (x_i = 2 pi i / nx, t_k = k / (nt - 1)): per
+    sample the phase phi ~ U(0, pi) and the diffusion coefficient alpha ~ U(1, 5) (the
+    distributions of the training set of the heat problem), IC g = sin(x_i + phi), and
+    u_hat = exp(-alpha t) sin(x + phi) + N(0, noise^2): the analytic solution the flow model
+    was trained on, perturbed.  Returns (u_hat [B, nt, nx], params [B, nx + 1] = [g, alpha])."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(nx) * (TWO_PI / nx)
+    t = np.arange(nt) / (nt - 1)
+    phi = rng.uniform(0.0, np.pi, size=B)
+    alpha = rng.uniform(1.0, 5.0, size=B)
+    g = np.sin(x[None, :] + phi[:, None])
+    u_hat = (np.exp(-alpha[:, None, None] * t[None, :, None]) * g[:, None, :]
+             + rng.normal(0.0, noise, size=(B, nt, nx)))
+    params = np.concatenate([g, alpha[:, None]], axis=1)
+    return np.ascontiguousarray(u_hat), np.ascontiguousarray(params)
+
+
 def gen_pcfm(seed, B, nx, nt, family="B"):
     """Inputs of one PCFM sampling pass on a 1-D family: the data sample x1 and the
     parameters from gen_1d (seed), the prior sample u0 ~ N(0, 1) and the perturbation
@@ -191,4 +212,5 @@ WORKLOADS = {
     "vorticity_2d": dict(B=512, N=16, nt=50, seed=1007),
     "burgers_bc_1d": dict(B=512, nx=101, nt=101, seed=1008),
     "burgers_flux_1d": dict(B=512, nx=101, nt=101, n_flux=5, seed=1009),
+    "heat2_1d": dict(B=512, nx=100, nt=100, seed=1010),
 }

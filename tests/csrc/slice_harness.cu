@@ -81,3 +81,11 @@ extern "C" void harness_df_op(int op, int n, const double *x, const double *y, d
 extern "C" void harness_split(int n, const double *x, float *h, float *l, int *ok) {
   for (int i = 0; i < n; ++i) ok[i] = df_split(x[i], h[i], l[i]) ? 1 : 0;
 }
+
+extern "C" void harness_split_trunc(int n, const double *x, float *h, float *l, int *ok) {
+  for (int i = 0; i < n; ++i) ok[i] = df_split_trunc(x[i], h[i], l[i]) ? 1 : 0;
+}
+
+extern "C" void harness_split_trunc_fast(int n, const double *x, float *h, float *l, int *ok) {
+  for (int i = 0; i < n; ++i) ok[i] = df_split_trunc_fast(x[i], h[i], l[i]) ? 1 : 0;
+}

@@ -33,6 +33,8 @@ def lib():
         L.harness_slice.argtypes = [C.c_int, dp, C.c_int, C.c_int, dp, ip, dp, ip, dp]
         L.harness_df_op.argtypes = [C.c_int, C.c_int, dp, dp, dp]
         L.harness_split.argtypes = [C.c_int, dp, fp, fp, ip]
+        L.harness_split_trunc.argtypes = [C.c_int, dp, fp, fp, ip]
+        L.harness_split_trunc_fast.argtypes = [C.c_int, dp, fp, fp, ip]
         _lib = L
     return _lib
 
@@ -104,6 +106,53 @@ def test_split_pair_exactness_and_range():
         err = abs(Fraction(float(h[i])) + Fraction(float(l[i])) - Fraction(x[i]))
         assert err <= Fraction(abs(x[i])) * Fraction(2) ** -47, (x[i], h[i], l[i])
         assert float(h[i]) == float(np.float32(x[i]))          # h = x rounded to float
+
+
+def test_fast_truncating_split_matches_truncating_split():
+    """The funnel-shift split gives the same pair as the truncating split wherever it accepts
+    (every value in range except zero, which it sends to the FP64 path)."""
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=20000) * np.exp(rng.uniform(-52, 41, size=20000))
+    x = np.concatenate([x, [0.0, -0.0, 1.0, -1.0, 2.0 ** -74, -(2.0 ** -74), 2.0 ** 57 * 1.5,
+                            np.nextafter(2.0 ** 58, 0), 2.0 ** 58, 2.0 ** -75, np.inf, np.nan]])
+    out = []
+    for fn in (lib().harness_split_trunc, lib().harness_split_trunc_fast):
+        h = np.zeros(len(x), np.float32)
+        l = np.zeros(len(x), np.float32)
+        ok = np.zeros(len(x), np.int32)
+        fn(len(x), x.ctypes.data_as(dp), h.ctypes.data_as(fp), l.ctypes.data_as(fp),
+           ok.ctypes.data_as(ip))
+        out.append((h, l, ok.astype(bool)))
+    (h0, l0, ok0), (h1, l1, ok1) = out
+    np.testing.assert_array_equal(ok1, ok0 & (x != 0))
+    np.testing.assert_array_equal(h1[ok1], h0[ok1])
+    np.testing.assert_array_equal(l1[ok1], l0[ok1])
+
+
+def test_truncating_split_exactness_and_range():
+    """The integer-only split: h = x truncated to 24 significant bits, |x - h - l| < 2^-46 |x|,
+    the same range as the rounding split; checked in exact rational arithmetic."""
+    rng = np.random.default_rng(2)
+    x = rng.normal(size=5000) * np.exp(rng.uniform(-45, 35, size=5000))
+    x = np.concatenate([x, [0.0, -0.0, 1.0, -1.0, 2.0 ** -74, -(2.0 ** -74), 2.0 ** 56,
+                            np.nextafter(2.0 ** 58, 0), 2.0 ** 58, 2.0 ** -75, np.inf, np.nan,
+                            1.999999999999, np.nextafter(2.0, 0), 1.0 + 2.0 ** -24,
+                            -(1.0 + 2.0 ** -52)]])
+    h = np.zeros(len(x), np.float32)
+    l = np.zeros(len(x), np.float32)
+    ok = np.zeros(len(x), np.int32)
+    lib().harness_split_trunc(len(x), x.ctypes.data_as(dp), h.ctypes.data_as(fp),
+                              l.ctypes.data_as(fp), ok.ctypes.data_as(ip))
+    ax = np.abs(x)
+    inrange = (ax == 0) | ((ax >= 2.0 ** -74) & (ax < 2.0 ** 58))
+    np.testing.assert_array_equal(ok.astype(bool), inrange)
+    for i in np.nonzero(ok)[0]:
+        xf = Fraction(x[i])
+        err = abs(Fraction(float(h[i])) + Fraction(float(l[i])) - xf)
+        assert err < abs(xf) * Fraction(2) ** -46 or err == 0, (x[i], h[i], l[i])
+        # h is x truncated toward zero to 24 significant bits
+        assert abs(Fraction(float(h[i]))) <= abs(xf)
+        assert abs(xf - Fraction(float(h[i]))) < abs(Fraction(float(h[i]))) * Fraction(2) ** -23 or x[i] == 0
 
 
 @pytest.mark.parametrize("mode", [0, 1])
