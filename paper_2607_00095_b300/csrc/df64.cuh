@@ -78,6 +78,19 @@ DF_INL df64 operator+(df64 x, df64 y) {
 DF_INL df64 operator-(df64 x) { return df64(-x.hi, -x.lo); }
 DF_INL df64 operator-(df64 x, df64 y) { return x + (-y); }
 
+// Sum with one error-free transformation, on the leading parts only (11 operations against 20):
+// the error is a few units of 2^-48 (|x| + |y|), the order of the inputs' own representation
+// errors, with no bound relative to the sum under cancellation.  For stencils and accumulations
+// whose operands are themselves double-float roundings.
+DF_INL df64 df_add_fast(df64 x, df64 y) {
+  const df64 s = df_two_sum(x.hi, y.hi);
+  return df_fast_two_sum(s.hi, s.lo + (x.lo + y.lo));
+}
+DF_INL df64 df_sub_fast(df64 x, df64 y) { return df_add_fast(x, df64(-y.hi, -y.lo)); }
+
+// x times a power of two s (exact while the result stays normal)
+DF_INL df64 df_scale2(df64 x, float s) { return df64(x.hi * s, x.lo * s); }
+
 DF_INL df64 operator*(df64 x, df64 y) {
   const float p = x.hi * y.hi;
   float e = fmaf(x.hi, y.hi, -p);
@@ -218,21 +231,34 @@ DF_INL bool df_split_trunc_fast(double x, float &h, float &l) {
   return (e - 949u) <= (1080u - 949u);
 }
 
-// float -> double by integer bit construction (normal floats and zero; other values go
-// through the conversion instruction)
+// The double -> double-float conversion for values outside the range of the integer splits,
+// kept out of line: inlined, the compiler predicates this rare fallback instead of branching
+// around it, and a predicated conversion still takes an issue slot of the FP64 pipe on every
+// call.
+static __host__ __device__ __noinline__ df64 df_from_double_slow(double x) { return df64(x); }
+
+// float -> double by integer operations only (no conversion instruction, which would take the
+// FP64 pipe): the exponent is rebiased 127 -> 1023 and the mantissa widened; a subnormal float
+// is normalised by its leading-zero count; zero, infinities and NaN payloads map bit for bit.
 DF_INL double df_f2d(float f) {
 #ifdef __CUDA_ARCH__
   const unsigned b = __float_as_uint(f);
   const unsigned ef = (b >> 23) & 0xFFu;
-  if (ef == 0u || ef == 0xFFu) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((ef + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
-  const unsigned lo = (b & 7u) << 29;
+  unsigned m = b & 0x7FFFFFu;
+  unsigned eh;
+  if (ef == 0u) {
+    const int p = 31 - __clz((int)m);            // leading bit of a subnormal (-1 for zero)
+    eh = m ? (unsigned)(p + 874) : 0u;           // 2^(p - 149), biased by 1023
+    m = m ? ((m << (23 - p)) & 0x7FFFFFu) : 0u;
+  } else {
+    eh = (ef == 0xFFu) ? 0x7FFu : ef + 896u;
+  }
+  const unsigned hi = (b & 0x80000000u) | (eh << 20) | (m >> 3);
+  const unsigned lo = (m & 7u) << 29;
   return __hiloint2double((int)hi, (int)lo);
 #else
   return (double)f;
 #endif
 }
-
-// df64 -> double with a single FP64 addition
 DF_INL double df_to_double(df64 x) { return df_f2d(x.hi) + df_f2d(x.lo); }
 DF_INL df64::operator double() const { return df_to_double(*this); }

@@ -15,12 +15,40 @@
 namespace {
 
 constexpr int T2D = 256;                 // threads per frame
-constexpr int REFINE = 4;                // float solves per right-hand side (refinement)
+constexpr int REFINE = 3;                // float solves per right-hand side (refinement)
 
 __device__ __forceinline__ df64 dsplit(double x) {
   float h, l;
   if (df_split(x, h, l)) return df64(h, l);
-  return df64(x);                        // out of the pair range: FP64 conversion
+  return df_from_double_slow(x);         // out of the pair range: FP64 conversion
+}
+
+// The same with integer operations only (truncating split, |x - hi - lo| < 2^-46 |x|), for the
+// per-element passes, which would otherwise load the FP64 pipe with one conversion per element
+__device__ __forceinline__ df64 isplit(double x) {
+  float h, l;
+  if (df_split_trunc(x, h, l)) return df64(h, l);
+  return df_from_double_slow(x);         // out of the pair range: FP64 conversion
+}
+
+// fn(e, x) for every element e of a frame's 2 N^2 doubles x = src[e] (thread-strided), with
+// FB loads in flight per thread before the first use (the passes are latency-bound otherwise)
+constexpr int FB = 8;
+template <int TOT, class Fn>
+__device__ __forceinline__ void frame_elems(const double *__restrict__ src, Fn &&fn) {
+  for (int e0 = threadIdx.x; e0 < TOT; e0 += T2D * FB) {
+    double x[FB];
+#pragma unroll
+    for (int b = 0; b < FB; ++b) {
+      const int e = e0 + b * T2D;
+      x[b] = e < TOT ? __ldg(src + e) : 0.0;
+    }
+#pragma unroll
+    for (int b = 0; b < FB; ++b) {
+      const int e = e0 + b * T2D;
+      if (e < TOT) fn(e, x[b]);
+    }
+  }
 }
 
 __device__ __forceinline__ float fabs_max(float a, float b) {
@@ -205,10 +233,13 @@ __device__ void fd_solve_tiled(float *rf, float *tf, const float *Q, const float
 // accuracy of the FP32 products (the dropped x_small y_small is below 2^-22 relative); the
 // double-float refinement against the exact stencil residual is unchanged.  Eight warps:
 // warp w computes rows 16 (w & 1) .. + 15 of the output of class w >> 1, all 32 columns.
+// x rounded to TF32 (10 mantissa bits), to nearest with ties away from zero, by integer
+// operations on the bit pattern: adding half a TF32 ulp to the magnitude bits carries into the
+// kept bits (and into the exponent when the mantissa overflows), the mask drops the rest.
+// Finite operands only (the class solve's are).  Integer ALU work: the conversion instruction
+// would take the FP64 pipe's issue slots on this GPU.
 __device__ __forceinline__ uint32_t fd_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
+  return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u;
 }
 
 __device__ __forceinline__ void fd_mma(float (&c)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -427,13 +458,14 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
     v.Rf[s] = v.Bh[s];
   }
   __syncthreads();
-  const df64 inv_scale = df64(1.0f, 0.0f) / scale;
+  // scale = 4 dx^2 and its inverse are powers of two (N is)
+  const float scale_f = scale.hi, inv_scale_f = 1.0f / scale.hi;
   for (int round = 0; round < REFINE; ++round) {
     if constexpr (M == 32) fd_solve_mma32(v.Rf, v.Tf, v.Q, v.Qt, v.I);
     else if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
     else fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
     for (int s = threadIdx.x; s < NN; s += T2D) {
-      const df64 zz = v.z(s) + scale * df64(v.Rf[s], 0.0f);
+      const df64 zz = df_add_fast(v.z(s), df64(v.Rf[s] * scale_f, 0.0f));
       v.Zh[s] = zz.hi;
       v.Zl[s] = zz.lo;
     }
@@ -443,10 +475,12 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
         const int c = s / MM, q = (s % MM) / M, p = s % M;
         const int base = c * MM;
         const df64 zc = v.z(s);
-        const df64 nb = v.z(base + q * M + (p + 1) % M) + v.z(base + q * M + (p + M - 1) % M) +
-                        v.z(base + ((q + 1) % M) * M + p) + v.z(base + ((q + M - 1) % M) * M + p);
-        const df64 az = (df64(4.0f, 0.0f) * zc - nb) * inv_scale;
-        const df64 r = df64(v.Bh[s], v.Bl[s]) - az;
+        const df64 nb = df_add_fast(df_add_fast(v.z(base + q * M + (p + 1) % M),
+                                                 v.z(base + q * M + (p + M - 1) % M)),
+                                     df_add_fast(v.z(base + ((q + 1) % M) * M + p),
+                                                 v.z(base + ((q + M - 1) % M) * M + p)));
+        const df64 az = df_scale2(df_sub_fast(df_scale2(zc, 4.0f), nb), inv_scale_f);
+        const df64 r = df_sub_fast(df64(v.Bh[s], v.Bl[s]), az);
         v.Rf[s] = r.hi + r.lo;
       }
       __syncthreads();
@@ -458,7 +492,7 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
   for (int c = 0; c < 4; ++c) g0[c] = v.z(c * MM);
   __syncthreads();
   for (int s = threadIdx.x; s < NN; s += T2D) {
-    const df64 zz = v.z(s) - g0[s / MM];
+    const df64 zz = df_sub_fast(v.z(s), g0[s / MM]);
     v.Zh[s] = zz.hi;
     v.Zl[s] = zz.lo;
   }
@@ -476,13 +510,56 @@ __device__ __forceinline__ df64 div_at(const double *w, int i, int j, const df64
   return ((ue - uw) + (vn - vs)) * h2;
 }
 
+// fn(e, x, y) with x = a[e], y = b[e] for every element e of two frame fields, batched as
+// frame_elems
+template <int TOT, class Fn>
+__device__ __forceinline__ void frame_elems2(const double *__restrict__ a,
+                                             const double *__restrict__ b, Fn &&fn) {
+  for (int e0 = threadIdx.x; e0 < TOT; e0 += T2D * FB) {
+    double x[FB], y[FB];
+#pragma unroll
+    for (int k = 0; k < FB; ++k) {
+      const int e = e0 + k * T2D;
+      x[k] = e < TOT ? __ldg(a + e) : 0.0;
+      y[k] = e < TOT ? __ldg(b + e) : 0.0;
+    }
+#pragma unroll
+    for (int k = 0; k < FB; ++k) {
+      const int e = e0 + k * T2D;
+      if (e < TOT) fn(e, x[k], y[k]);
+    }
+  }
+}
+
+// (D x)(i, j) of a field held as float pairs in shared memory, xp[2][N][N]
+template <int M>
+__device__ __forceinline__ df64 div_at_pairs(const float2 *xp, int i, int j, const df64 &h2) {
+  constexpr int N = 2 * M, NN = N * N;
+  const float2 ue = xp[j * N + (i + 1) % N], uw = xp[j * N + (i + N - 1) % N];
+  const float2 vn = xp[NN + ((j + 1) % N) * N + i], vs = xp[NN + ((j + N - 1) % N) * N + i];
+  return df_scale2(df_add_fast(df_sub_fast(df64(ue.x, ue.y), df64(uw.x, uw.y)),
+                               df_sub_fast(df64(vn.x, vn.y), df64(vs.x, vs.y))), h2.hi);
+}
+
+// (D w)(i, j) of a field held as doubles in shared memory, component 0 in w0, 1 in w1
+template <int M>
+__device__ __forceinline__ df64 div_at_smem(const double *w0, const double *w1, int i, int j,
+                                            const df64 &h2) {
+  constexpr int N = 2 * M;
+  const df64 ue = isplit(w0[j * N + (i + 1) % N]);
+  const df64 uw = isplit(w0[j * N + (i + N - 1) % N]);
+  const df64 vn = isplit(w1[((j + 1) % N) * N + i]);
+  const df64 vs = isplit(w1[((j + N - 1) % N) * N + i]);
+  return df_scale2(df_add_fast(df_sub_fast(ue, uw), df_sub_fast(vn, vs)), h2.hi);
+}
+
 // (D^T z) for element e of w[2][N][N] (component e / N^2)
 template <int M>
 __device__ __forceinline__ df64 divT_at(const View2D<M> &v, int e, const df64 &h2) {
   constexpr int N = 2 * M, NN = N * N;
   const int comp = e / NN, cell = e % NN, i = cell % N, j = cell / N;
-  if (comp == 0) return (v.z(cell_slot<M>(i - 1, j)) - v.z(cell_slot<M>(i + 1, j))) * h2;
-  return (v.z(cell_slot<M>(i, j - 1)) - v.z(cell_slot<M>(i, j + 1))) * h2;
+  if (comp == 0) return df_scale2(df_sub_fast(v.z(cell_slot<M>(i - 1, j)), v.z(cell_slot<M>(i + 1, j))), h2.hi);
+  return df_scale2(df_sub_fast(v.z(cell_slot<M>(i, j - 1)), v.z(cell_slot<M>(i, j + 1))), h2.hi);
 }
 
 // Forward projection of frame f of one sample by the whole block (T2D threads, every thread
@@ -490,6 +567,12 @@ __device__ __forceinline__ df64 divT_at(const View2D<M> &v, int e, const df64 &h
 // (K0, r2), lam_s the sample's multipliers (nt N^2 divergence rows, then nt energy rows).
 // The block's dynamic shared memory (Smem2D<M>::bytes) is passed in v; *out receives the
 // frame's statistics (written by thread 0).
+//
+// Global memory is touched by batched loads only (frame_elems): w_hat is read once into shared
+// memory as float pairs for the divergence stencil (in the Poisson work area, which is free
+// until the solve) and twice more, batched, by the element passes after the solve; the written
+// w is kept in shared memory (in the right-hand-side and product areas, free after the solve)
+// for the residual of the written field.
 template <int M>
 __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
                                 const double *__restrict__ pr, int f, int nt,
@@ -505,17 +588,20 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
     v.I[i] = Ig[i];
     v.Qt[(i % M) * M + i / M] = Qg[i];
   }
-  __syncthreads();
-  // b = D w_hat on every cell; moments of w_hat
+  // w_hat as float pairs in the Poisson work area (z hi / lo, r, t: 4 N^2 floats = 2 N^2 pairs)
+  float2 *xp = reinterpret_cast<float2 *>(v.Zh);
   df64 a0(0.0f, 0.0f);
+  frame_elems<2 * NN>(src, [&](int e, double xd) {
+    const df64 x = isplit(xd);
+    xp[e] = make_float2(x.hi, x.lo);
+    a0 = df_add_fast(a0, x * x);
+  });
+  __syncthreads();
+  // b = D w_hat on every cell
   float d2 = 0.0f, dinf = 0.0f;
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 x = dsplit(src[e]);
-    a0 = a0 + x * x;
-  }
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
-    const df64 dv = div_at<M>(src, i, j, h2);
+    const df64 dv = div_at_pairs<M>(xp, i, j, h2);
     const int s = cell_slot<M>(i, j);
     v.Bh[s] = dv.hi;
     v.Bl[s] = dv.lo;
@@ -526,16 +612,19 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   }
   __syncthreads();
   poisson_frame<M>(v, scale);
-  // y = D^T z and its moments
+  // y = D^T z, kept as float pairs in the right-hand-side and product areas (free after the
+  // solve; component 0 over b hi / lo, component 1 over r / t), and its moments.  The
+  // extremes are stopping-test bounds, formed from the leading parts.
+  float2 *y0 = reinterpret_cast<float2 *>(v.Bh), *y1 = reinterpret_cast<float2 *>(v.Rf);
   df64 a2(0.0f, 0.0f);
   float pinf = 0.0f, yinf = 0.0f;
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
+  frame_elems<2 * NN>(src, [&](int e, double xd) {
     const df64 y = divT_at<M>(v, e, h2);
-    a2 = a2 + y * y;
+    if (e < NN) y0[e] = make_float2(y.hi, y.lo); else y1[e - NN] = make_float2(y.hi, y.lo);
+    a2 = df_add_fast(a2, y * y);
     yinf = fabs_max(yinf, y.hi);
-    const df64 pw = dsplit(src[e]) - y;
-    pinf = fabs_max(pinf, pw.hi);
-  }
+    pinf = fabs_max(pinf, isplit(xd).hi - y.hi);
+  });
   a0 = block_sumdf(a0, v.red);
   a2 = block_sumdf(a2, v.red);
   d2 = block_sumf(d2, v.red);
@@ -565,21 +654,30 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   __syncthreads();
   const df64 A(zs[0], zs[1]), S(zs[2], zs[3]), MU(zs[4], zs[5]), KAP(zs[6], zs[7]), AL(zs[8], zs[9]);
   const df64 Cc = S - A;
-  // write w = a w_hat + c y, lambda_div = mu z; exact residual pieces
-  float ginf = 0.0f, obj = 0.0f;
-  df64 w2(0.0f, 0.0f);
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 y = divT_at<M>(v, e, h2);
-    const df64 x = dsplit(src[e]);
-    const df64 w = A * x + Cc * y;
+  // write w = a w_hat + c y (global memory, and in shared memory over its own y), lambda_div
+  // = mu z.  On the moment family w = a x + c y the gradient of the Lagrangian is
+  // alpha w - x + mu y = p x + r y with the frame's scalar residuals p = alpha a - 1 and
+  // r = alpha c + mu (formed in double-float), so ||grad L||_inf comes from the leading parts
+  // of x and y; ||w - x||^2 and ||w||^2 follow from the moments (x . y = ||y||^2: y is the
+  // orthogonal projection of x onto the range of D_a^T).
+  double *w0 = reinterpret_cast<double *>(v.Bh);   // component 0: b hi / lo area (N^2 doubles)
+  double *w1 = reinterpret_cast<double *>(v.Rf);   // component 1: r / t area (N^2 doubles)
+  const df64 one(1.0f, 0.0f);
+  const float pg = (AL * A - one).hi, rg = (AL * Cc + MU).hi;
+  float ginf = 0.0f;
+  frame_elems<2 * NN>(src, [&](int e, double xd) {
+    const float2 yp = (e < NN) ? y0[e] : y1[e - NN];
+    const df64 y(yp.x, yp.y);
+    const df64 x = isplit(xd);
+    const df64 w = df_add_fast(A * x, Cc * y);
     const double wd = df_to_double(w);
     dst[e] = wd;
-    const df64 gl = AL * w - x + MU * y;
-    ginf = fabs_max(ginf, gl.hi);
-    const float dwv = (w - x).hi;
-    obj = fmaf(dwv, dwv, obj);
-    w2 = w2 + w * w;
-  }
+    if (e < NN) w0[e] = wd; else w1[e - NN] = wd;
+    ginf = fabs_max(ginf, fmaf(pg, x.hi, rg * y.hi));
+  });
+  const df64 am1 = A - one;
+  const df64 obj2 = am1 * am1 * a0 + (df64(2.0f, 0.0f) * am1 * Cc + Cc * Cc) * a2;
+  const df64 w2 = A * A * a0 + (df64(2.0f, 0.0f) * A * Cc + Cc * Cc) * a2;
   double *lb = lam_s + (size_t)f * NN;
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
@@ -589,13 +687,11 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   float hinf_all = 0.0f, hinf_act = 0.0f;
   for (int cell = threadIdx.x; cell < NN; cell += T2D) {
     const int i = cell % N, j = cell / N;
-    const float dv = div_at<M>(dst, i, j, h2).hi;   // the written w (block-visible after the barrier)
+    const float dv = div_at_smem<M>(w0, w1, i, j, h2).hi;   // the written w
     hinf_all = fabs_max(hinf_all, dv);
     if (!(i < 2 && j < 2)) hinf_act = fabs_max(hinf_act, dv);
   }
   ginf = block_max(ginf, v.red);
-  obj = block_sumf(obj, v.red);
-  w2 = block_sumdf(w2, v.red);
   hinf_all = block_max(hinf_all, v.red);
   hinf_act = block_max(hinf_act, v.red);
   if (threadIdx.x == 0) {
@@ -609,9 +705,97 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
     st.kkt_inf = (double)fmaxf(fmaxf(ginf, hinf_act), hk);
     st.h_inf = (double)fmaxf(hinf_all, hk);
     if (hK.hi != hK.hi || ginf != ginf) { st.kkt_inf = NAN; st.h_inf = NAN; }
-    st.obj = 0.5 * (double)obj;
+    st.obj = 0.5 * df_to_double(obj2);
     *out = st;
     lam_s[(size_t)nt * NN + f] = df_to_double(KAP);
+  }
+}
+
+// Adjoint of frame f of one sample by the whole block (T2D threads, every thread must call
+// it).  At the solution D_a w = 0, so S = J W^-1 J^T is block diagonal:
+// (1/alpha) diag(D_a D_a^T, dx^4 ||w||^2).  Hence b_div = (D_a D_a^T)^-1 D_a gbar (one Poisson
+// solve), b_K = w^T gbar / (dx^2 ||w||^2), a = (gbar - D_a^T b_div - b_K dx^2 w) / alpha.
+// gsrc / wsrc are the frame's dL/dw and w [2][N][N], kap its energy multiplier, pr the
+// sample's parameters (K0, r2); writes a into dst (NaN when bad) and the frame's contribution
+// to dL/d(K0, r2) into *contrib (thread 0).
+template <int M>
+__device__ void frame2d_backward(View2D<M> &v, const double *__restrict__ gsrc,
+                                 const double *__restrict__ wsrc, double kap,
+                                 const double *__restrict__ pr, int f, int nt, bool bad,
+                                 const float *__restrict__ Qg, const float *__restrict__ Ig,
+                                 double *__restrict__ dst, BwdContrib *__restrict__ contrib) {
+  constexpr int N = 2 * M, NN = N * N, MM = M * M;
+  const df64 h2((float)N * 0.5f, 0.0f);
+  const df64 dx(1.0 / N);
+  const df64 scale = df64(4.0 / ((double)N * (double)N));
+  for (int i = threadIdx.x; i < MM; i += T2D) {
+    v.Q[i] = Qg[i];
+    v.I[i] = Ig[i];
+    v.Qt[(i % M) * M + i / M] = Qg[i];
+  }
+  // gbar as float pairs in the Poisson work area for the divergence stencil (as the forward)
+  float2 *gp2 = reinterpret_cast<float2 *>(v.Zh);
+  df64 dot(0.0f, 0.0f), ww(0.0f, 0.0f);
+  frame_elems2<2 * NN>(wsrc, gsrc, [&](int e, double wd, double gd) {
+    const df64 x = isplit(wd), gx = isplit(gd);
+    gp2[e] = make_float2(gx.hi, gx.lo);
+    dot = df_add_fast(dot, x * gx);
+    ww = df_add_fast(ww, x * x);
+  });
+  __syncthreads();
+  for (int cell = threadIdx.x; cell < NN; cell += T2D) {
+    const int i = cell % N, j = cell / N;
+    const df64 dv = div_at_pairs<M>(gp2, i, j, h2);
+    const int s = cell_slot<M>(i, j);
+    v.Bh[s] = dv.hi;
+    v.Bl[s] = dv.lo;
+  }
+  __syncthreads();
+  poisson_frame<M>(v, scale);
+  dot = block_sumdf(dot, v.red);
+  ww = block_sumdf(ww, v.red);
+  const df64 dx2 = dx * dx;
+  const df64 alpha = df64(1.0f, 0.0f) + dsplit(kap) * dx2;
+  const df64 bK = dot / (dx2 * ww);
+  const df64 ialpha = df64(1.0f, 0.0f) / alpha;
+  const df64 bKdx2 = bK * dx2;
+  frame_elems2<2 * NN>(gsrc, wsrc, [&](int e, double gd, double wd) {
+    const df64 y = divT_at<M>(v, e, h2);
+    const df64 a = df_sub_fast(df_sub_fast(isplit(gd), y), bKdx2 * isplit(wd)) * ialpha;
+    dst[e] = bad ? NAN : df_to_double(a);
+  });
+  if (threadIdx.x == 0) {
+    const double t = (double)f / (double)(nt - 1);
+    const double ex = exp(-pr[1] * t);
+    const double bk = df_to_double(bK);
+    // h_K = 1/2 dx^2 ||w||^2 - K0 exp(-r2 t): dL/dK0 += b_K e, dL/dr2 += -b_K t K0 e
+    *contrib = BwdContrib{bk * ex, -bk * t * pr[0] * ex, 0.0, 0.0};
+  }
+}
+
+// dL/d(K0, r2) of one sample from its nt frame contributions c[0..nt) (one warp, fixed order,
+// so the bits do not depend on which warp runs it); kCoherent reads through L2 only
+// (contributions written by other blocks of a running kernel).
+template <bool kCoherent>
+__device__ __forceinline__ void frame2d_param_grad(const BwdContrib *__restrict__ c, int nt,
+                                                   bool bad, double *__restrict__ gp, int lane) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int f = lane; f < nt; f += 32) {
+    if (kCoherent) {
+      s0 += __ldcg(&c[f].bm);
+      s1 += __ldcg(&c[f].bex);
+    } else {
+      s0 += c[f].bm;
+      s1 += c[f].bex;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+  }
+  if (lane == 0) {
+    gp[0] = bad ? NAN : s0;
+    gp[1] = bad ? NAN : s1;
   }
 }
 

@@ -5,7 +5,8 @@
 //     S b = J W^-1 gbar,   a = W^-1 (gbar - J^T b),   S = J W^-1 J^T.
 // J W^-1 gbar needs the interior sums sum gbar_i and sum u_i gbar_i (and, when the forward
 // factor is not cached, sum u_i and sum u_i^2 to rebuild S), so the kernel mirrors the forward:
-//   phase 1  (4 lanes per slice): float-pair split of u and gbar, double-float sums;
+//   phase 1  (4 lanes per slice): float-pair split of u and gbar with integer operations only
+//            (|x - hi - lo| <= 2^-48 |x|), double-float sums;
 //   phase 2  (one slice per lane): S b = v in double-float, from the cached FP64 LDL^T factor
 //            or from S rebuilt in double-float; the per-slice contributions to dL/dtheta;
 //   phase 3  (4 lanes per slice): a_i = gbar_i / w - (dx b_m + 2 dx u_i b_e) / w with two
@@ -105,10 +106,10 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
             const int i = i0 + 8 * c;
             if (i >= nx) break;
             float uh0, ul0, uh1, ul1, gh0, gl0, gh1, gl1;
-            ok &= df_split(vu[c].x, uh0, ul0);
-            ok &= df_split(vu[c].y, uh1, ul1);
-            ok &= df_split(vg[c].x, gh0, gl0);
-            ok &= df_split(vg[c].y, gh1, gl1);
+            ok &= df_split_trunc(vu[c].x, uh0, ul0);
+            ok &= df_split_trunc(vu[c].y, uh1, ul1);
+            ok &= df_split_trunc(vg[c].x, gh0, gl0);
+            ok &= df_split_trunc(vg[c].y, gh1, gl1);
             if (i == 0 || i == ih) { uh0 = ul0 = gh0 = gl0 = 0.0f; }
             if (i + 1 == ih) { uh1 = ul1 = gh1 = gl1 = 0.0f; }
             acc2(sg, eg, gh0, gl0);

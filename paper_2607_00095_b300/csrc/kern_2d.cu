@@ -157,9 +157,7 @@ k2d_frame(int B, int nt, const double *__restrict__ wh, const double *__restrict
 
 namespace {
 
-// Adjoint of one frame.  At the solution D_a w = 0, so S = J W^-1 J^T is block diagonal:
-// (1/alpha) diag(D_a D_a^T, dx^4 ||w||^2).  Hence b_div = (D_a D_a^T)^-1 D_a gbar (one Poisson
-// solve), b_K = w^T gbar / (dx^2 ||w||^2), a = (gbar - D_a^T b_div - b_K dx^2 w) / alpha.
+// Adjoint of the frames of a batch, one block per frame (frame2d_backward, frame_2d.cuh).
 template <int M>
 __global__ void __launch_bounds__(T2D)
 k2d_frame_bwd(int B, int nt, const double *__restrict__ gw, const double *__restrict__ w,
@@ -167,61 +165,17 @@ k2d_frame_bwd(int B, int nt, const double *__restrict__ gw, const double *__rest
               const snap_stats *__restrict__ fst, const float *__restrict__ Qg,
               const float *__restrict__ Ig, double *__restrict__ gout,
               BwdContrib *__restrict__ contrib) {
-  constexpr int N = 2 * M, NN = N * N, MM = M * M;
+  constexpr int NN = 4 * M * M;
   extern __shared__ __align__(16) unsigned char smem2d[];
   View2D<M> v(smem2d);
   const int fr = blockIdx.x;
   if (fr >= B * nt) return;
   const int b = fr / nt, f = fr % nt;
-  const int n_rows = nt * NN + nt;
-  const double *gsrc = gw + (size_t)fr * 2 * NN;
-  const double *wsrc = w + (size_t)fr * 2 * NN;
-  const df64 h2((float)N * 0.5f, 0.0f);
-  const df64 dx(1.0 / N);
-  const df64 scale = df64(4.0 / ((double)N * (double)N));
-  for (int i = threadIdx.x; i < MM; i += T2D) {
-    v.Q[i] = Qg[i];
-    v.I[i] = Ig[i];
-    v.Qt[(i % M) * M + i / M] = Qg[i];
-  }
-  __syncthreads();
-  df64 dot(0.0f, 0.0f), ww(0.0f, 0.0f);
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 x = dsplit(wsrc[e]), gx = dsplit(gsrc[e]);
-    dot = dot + x * gx;
-    ww = ww + x * x;
-  }
-  for (int cell = threadIdx.x; cell < NN; cell += T2D) {
-    const int i = cell % N, j = cell / N;
-    const df64 dv = div_at<M>(gsrc, i, j, h2);
-    const int s = cell_slot<M>(i, j);
-    v.Bh[s] = dv.hi;
-    v.Bl[s] = dv.lo;
-  }
-  __syncthreads();
-  poisson_frame<M>(v, scale);
-  dot = block_sumdf(dot, v.red);
-  ww = block_sumdf(ww, v.red);
-  const double kap = lam[(size_t)b * n_rows + (size_t)nt * NN + f];
-  const df64 dx2 = dx * dx;
-  const df64 alpha = df64(1.0f, 0.0f) + dsplit(kap) * dx2;
-  const df64 bK = dot / (dx2 * ww);
-  const df64 ialpha = df64(1.0f, 0.0f) / alpha;
+  const size_t n_rows = (size_t)nt * NN + nt;
   const bool bad = fst && fst[b].status != SNAP_SAMPLE_OK;
-  double *dst = gout + (size_t)fr * 2 * NN;
-  for (int e = threadIdx.x; e < 2 * NN; e += T2D) {
-    const df64 y = divT_at<M>(v, e, h2);
-    const df64 a = (dsplit(gsrc[e]) - y - bK * dx2 * dsplit(wsrc[e])) * ialpha;
-    dst[e] = bad ? NAN : df_to_double(a);
-  }
-  if (threadIdx.x == 0) {
-    const double *pr = params + (size_t)b * 2;
-    const double t = (double)f / (double)(nt - 1);
-    const double ex = exp(-pr[1] * t);
-    const double bk = df_to_double(bK);
-    // h_K = 1/2 dx^2 ||w||^2 - K0 exp(-r2 t): dL/dK0 += b_K e, dL/dr2 += -b_K t K0 e
-    contrib[fr] = BwdContrib{bk * ex, -bk * t * pr[0] * ex, 0.0, 0.0};
-  }
+  frame2d_backward<M>(v, gw + (size_t)fr * 2 * NN, w + (size_t)fr * 2 * NN,
+                      lam[(size_t)b * n_rows + (size_t)nt * NN + f], params + (size_t)b * 2, f,
+                      nt, bad, Qg, Ig, gout + (size_t)fr * 2 * NN, contrib + fr);
 }
 
 __global__ void k2d_backward_params(int B, int nt, const snap_stats *__restrict__ fst,
@@ -230,21 +184,8 @@ __global__ void k2d_backward_params(int B, int nt, const snap_stats *__restrict_
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (warp >= B) return;
-  double s0 = 0.0, s1 = 0.0;
-  for (int f = lane; f < nt; f += 32) {
-    const BwdContrib c = contrib[(size_t)warp * nt + f];
-    s0 += c.bm;
-    s1 += c.bex;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-  }
-  if (lane == 0) {
-    const bool bad = fst && fst[warp].status != SNAP_SAMPLE_OK;
-    gp[(size_t)warp * 2] = bad ? NAN : s0;
-    gp[(size_t)warp * 2 + 1] = bad ? NAN : s1;
-  }
+  const bool bad = fst && fst[warp].status != SNAP_SAMPLE_OK;
+  frame2d_param_grad<false>(contrib + (size_t)warp * nt, nt, bad, gp + (size_t)warp * 2, lane);
 }
 
 // h(w) of every nominal row of one frame (FP64; a verification kernel)

@@ -549,20 +549,45 @@ DF_INL void slice_newton_h(const SliceIn<T> &d, const SliceIn<float> &d32, Slice
 
 // Polishing step after the stopping test (reading R27): the test bounds ||h||, and the
 // multipliers only through the conditioning of S, which is large on slices whose boundary
-// circle is nearly degenerate (c_k ~ 1e-6: S ~ 1e7 there).  One more Newton step with the
-// Schur system assembled and solved in double-float (not float) leaves the multipliers at
-// the rounding level; it is kept when it does not increase ||h||_inf.
-DF_INL void slice_polish_df64(const SliceIn<df64> &d, SliceZ<df64> &z, SliceH<df64> &e,
-                              SliceResult &R) {
+// circle is nearly degenerate (c_k ~ 1e-6: S ~ 1e7 there).  One more Newton step leaves the
+// multipliers at the rounding level.  S is first factored in float at the float image of z:
+// when its pivots over the rows present are within a factor 1e3 of each other and its
+// multipliers l are below 1e2 (S well conditioned), the step is solved in float against the
+// double-float residual (one more step of iterative refinement, error factor ~ kappa 2^-24);
+// otherwise S is assembled, factored and solved in double-float.  The step is kept when it
+// does not increase ||h||_inf and leaves W positive.
+DF_INL void slice_polish(const SliceIn<df64> &d, const SliceIn<float> &d32, SliceZ<df64> &z,
+                         SliceH<df64> &e) {
   const df64 zero(0.0f, 0.0f), one(1.0f, 0.0f);
   if (!(e.alpha > zero) || !(e.beta > zero)) return;
-  df64 s00, s01, s02, s11, s12, s22;
-  slice_schur(d, z, e.su, e.su2, one / e.alpha, one / e.beta, s00, s01, s02, s11, s12, s22);
-  Ldl3<df64> f;
-  if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) return;
+  const bool hm = d.rows & SL_MASS, he = d.rows & SL_ENERGY, hb = d.rows & SL_BOUND;
+  const SliceZ<float> zf{z.a.hi, z.c.hi, z.p0.hi, z.ph.hi, z.lm.hi, z.le.hi, z.lb.hi};
+  float f00, f01, f02, f11, f12, f22;
+  slice_schur(d32, zf, e.su.hi, e.su2.hi, df_rcp(e.alpha.hi), df_rcp(e.beta.hi), f00, f01, f02,
+              f11, f12, f22);
+  Ldl3<float> ff;
+  bool cheap = false;
+  if (ldl3_factor(f00, f01, f02, f11, f12, f22, ff)) {
+    const float a0 = fabsf(ff.d0), a1 = fabsf(ff.d1), a2 = fabsf(ff.d2);
+    const float dmax = fmaxf(hm ? a0 : 0.0f, fmaxf(he ? a1 : 0.0f, hb ? a2 : 0.0f));
+    const float dmin = fminf(hm ? a0 : INFINITY, fminf(he ? a1 : INFINITY, hb ? a2 : INFINITY));
+    const float lmax = fmaxf(fabsf(ff.l10), fmaxf(fabsf(ff.l20), fabsf(ff.l21)));
+    cheap = dmax <= 1e3f * dmin && lmax <= 1e2f;
+  }
   df64 dlm, dle, dlb;
-  ldl3_solve(f, (d.rows & SL_MASS) ? e.hm : zero, (d.rows & SL_ENERGY) ? e.he : zero,
-             (d.rows & SL_BOUND) ? e.hb : zero, dlm, dle, dlb);
+  if (cheap) {
+    float xm, xe, xb;
+    ldl3_solve(ff, hm ? e.hm.hi : 0.0f, he ? e.he.hi : 0.0f, hb ? e.hb.hi : 0.0f, xm, xe, xb);
+    dlm = df64(xm, 0.0f);
+    dle = df64(xe, 0.0f);
+    dlb = df64(xb, 0.0f);
+  } else {
+    df64 s00, s01, s02, s11, s12, s22;
+    slice_schur(d, z, e.su, e.su2, one / e.alpha, one / e.beta, s00, s01, s02, s11, s12, s22);
+    Ldl3<df64> f;
+    if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) return;
+    ldl3_solve(f, hm ? e.hm : zero, he ? e.he : zero, hb ? e.hb : zero, dlm, dle, dlb);
+  }
   SliceZ<df64> zt;
   zt.lm = z.lm + dlm;
   zt.le = z.le + dle;
@@ -574,6 +599,35 @@ DF_INL void slice_polish_df64(const SliceIn<df64> &d, SliceZ<df64> &z, SliceH<df
     z = zt;
     e = et;
   }
+}
+
+// The full residual (grad_u L included) at z from the row residuals h already evaluated there
+// (the same values slice_eval forms): the gradient coefficients P, Q, g0, gh in double-float,
+// phi and ||F||_inf from their float images.
+DF_INL void slice_eval_from_h(const SliceIn<df64> &d, const SliceZ<df64> &z,
+                              const SliceH<df64> &h, SliceEval<df64> &e) {
+  const df64 one(1.0f, 0.0f);
+  e.alpha = h.alpha;
+  e.beta = h.beta;
+  e.su = h.su;
+  e.su2 = h.su2;
+  e.hm = h.hm;
+  e.he = h.he;
+  e.hb = h.hb;
+  e.P = e.alpha * z.a - one;
+  e.Q = e.alpha * z.c + d.dx * z.lm;
+  e.g0 = e.beta * z.p0 - d.uh0 + d.dx * z.lm;
+  e.gh = e.beta * z.ph - d.uhh + d.dx * z.lm;
+  const float P = e.P.hi, Q = e.Q.hi, g0 = e.g0.hi, gh = e.gh.hi;
+  const float hm = e.hm.hi, he = e.he.hi, hb = e.hb.hi;
+  float gi2 = P * P * d.S2.hi + 2.0f * P * Q * d.S1.hi + Q * Q * d.n.hi;
+  if (gi2 < 0.0f) gi2 = 0.0f;
+  const float phi = 0.5f * (gi2 + g0 * g0 + gh * gh + hm * hm + he * he + hb * hb);
+  float r = fmaxf(fabsf(P * d.mx.hi + Q), fabsf(P * d.mn.hi + Q));
+  r = fmaxf(r, fmaxf(fmaxf(fabsf(g0), fabsf(gh)), fmaxf(fmaxf(fabsf(hm), fabsf(he)), fabsf(hb))));
+  if (phi != phi) r = phi;
+  e.phi = df64(phi, 0.0f);
+  e.res = df64(r, 0.0f);
 }
 
 // Start of the multiplier iteration inside the region W > 0, where the KKT point is unique
@@ -650,9 +704,9 @@ DF_INL SliceResult slice_solve_mixed(const SliceIn<df64> &dd, SliceZ<df64> &z,
   slice_eval_h(dd, z, eh);
   slice_newton_h<df64>(dd, d32, z, eh, sf.tol, c1x2, wk1, sf.cap, o.max_backtracks,
                        o.max_iter - R.iters, R);
-  if (R.status == SNAP_SAMPLE_OK) slice_polish_df64(dd, z, eh, R);
+  if (R.status == SNAP_SAMPLE_OK) slice_polish(dd, d32, z, eh);
   // the full residual (grad_u L included) at the returned point
-  slice_eval(dd, z, e);
+  slice_eval_from_h(dd, z, eh, e);
   if (R.status == SNAP_SAMPLE_OK && !(e.res <= sd.tol)) R.status = SNAP_SAMPLE_MAXITER;
   if (R.status == SNAP_SAMPLE_OK && !(e.alpha > df64(0.0f, 0.0f) && e.beta > df64(0.0f, 0.0f))) {
     // W not positive definite: second-order check by the inertia of K
