@@ -659,6 +659,24 @@ def measure_uneven(dev, reps=30):
     g.replay()
     ms_g = _event_ms(g.replay, reps)
     conv_g = converged()
+    # the adjoint of the mix (dL/du ~ N(0, 1)): one persistent launch (owned graph) against one
+    # snap_project_backward launch per group (the same calls captured in a graph)
+    b.launch_graph()
+    gbufs = b.alloc_backward(dev)
+    for pi, gb in gbufs.items():
+        gb["gu"].copy_(torch.as_tensor(np.stack([synthetic.gen_gbar(2004 + int(i), mix[i]["u_hat"].size)
+                                                 for i in gb["ids"]])))
+    b.capture_graph_backward()
+    b.launch_graph_backward()
+    bms_p = _event_ms(b.launch_graph_backward, reps)
+    b.backward_grouped()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(cap):
+        gbw = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gbw, stream=cap):
+            b.backward_grouped(stream=cap)
+    gbw.replay()
+    bms_g = _event_ms(gbw.replay, reps)
     return {"workload": "uneven", "instances": n, "groups": len(keys),
             "schedule": sched, "autotune_best_ms": tune_ms,
             "persistent_ms_per_call": ms_p, "grouped_ms_per_call": ms_g,
@@ -669,6 +687,8 @@ def measure_uneven(dev, reps=30):
             "latency_us_p50": float(np.percentile(lat_us, 50)),
             "latency_us_p99": float(np.percentile(lat_us, 99)),
             "makespan_us": makespan_us, "input_bytes": in_bytes,
+            "backward_persistent_ms_per_call": bms_p, "backward_grouped_ms_per_call": bms_g,
+            "backward_speedup_vs_grouped": bms_g / bms_p,
             "persistent_launches_per_call": 1,
             "grouped_launches_per_call": sum(2 if f == "C" else 3 for f, _, _ in keys)}
 

@@ -444,6 +444,34 @@ SNAP_API snap_status snap_batch_capture_graph(snap_batch_t b, const snap_options
                                               size_t workspace_bytes);
 SNAP_API snap_status snap_batch_launch_graph(snap_batch_t b, snap_stream_t stream);
 
+/* ---- adjoint of an uneven batch ----
+ * The implicit-function adjoint of every bound instance (the per-instance operation of
+ * snap_project_backward, Appendix B's KKT system at the solution) in ONE persistent launch:
+ * the forward's work lists and schedule, 1-D tiles per warp and 2-D frames per block, each
+ * instance's dL/dparams formed by the last of its units to finish (fixed order: the bits of
+ * the per-group launches).  The forward binding supplies u (the solution), lambda, params and
+ * stats (a sample whose forward status is not OK gets NaN gradients); the backward binding
+ * below supplies, per instance, dL/du (input, n_vars doubles), dL/du_hat (output, n_vars) and
+ * dL/dparams (output, n_params, or NULL: not formed; grad_params itself may be NULL).  1-D
+ * instances need dL/du and dL/du_hat 16-byte aligned, 2-D 8-byte; the pointer table is copied
+ * to the device, the caller keeps ownership.  The workspace is snap_batch_workspace_size's.
+ * Errors: INVALID_ARG (null or misaligned), NOT_READY (forward or backward binding missing),
+ * WORKSPACE, CUDA. */
+SNAP_API snap_status snap_batch_bind_backward(snap_batch_t b, const double *const *grad_u,
+                                              double *const *grad_u_hat,
+                                              double *const *grad_params);
+SNAP_API snap_status snap_batch_project_backward(snap_batch_t b, void *workspace,
+                                                 size_t workspace_bytes, snap_stream_t stream);
+/* The same adjoint as plain snap_project_backward launches, one per group (the comparison
+ * baseline); every group's buffers of both bindings contiguous, else UNSUPPORTED. */
+SNAP_API snap_status snap_batch_project_backward_grouped(snap_batch_t b, void *workspace,
+                                                         size_t workspace_bytes,
+                                                         snap_stream_t stream);
+/* Capture snap_batch_project_backward into a CUDA graph owned by the batch / launch it. */
+SNAP_API snap_status snap_batch_capture_graph_backward(snap_batch_t b, void *workspace,
+                                                       size_t workspace_bytes);
+SNAP_API snap_status snap_batch_launch_graph_backward(snap_batch_t b, snap_stream_t stream);
+
 /* Shape of the batch: groups, 1-D tiles and 2-D frames in the current schedule's queues. */
 SNAP_API snap_status snap_batch_info(snap_batch_t b, int *n_groups, int *n_tiles_1d,
                                      int *n_frames_2d);

@@ -86,6 +86,11 @@ _PROTOS = {
     "snap_batch_capture_graph": (C.c_int, [_vp, C.POINTER(Options), _vp, _vp, C.c_size_t]),
     "snap_batch_launch_graph": (C.c_int, [_vp, _vp]),
     "snap_batch_info": (C.c_int, [_vp, _ip, _ip, _ip]),
+    "snap_batch_bind_backward": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp)]),
+    "snap_batch_project_backward": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
+    "snap_batch_project_backward_grouped": (C.c_int, [_vp, _vp, C.c_size_t, _vp]),
+    "snap_batch_capture_graph_backward": (C.c_int, [_vp, _vp, C.c_size_t]),
+    "snap_batch_launch_graph_backward": (C.c_int, [_vp, _vp]),
     "snap_measure_fp64_rate": (C.c_int, [C.c_int, _dp]),
     "snap_last_launch_count": (C.c_int, []),
     "snap_profile_enable": (C.c_int, [C.c_int]),

@@ -390,6 +390,56 @@ class Batch:
     def launch_graph(self, stream=None):
         check(lib().snap_batch_launch_graph(self._h, _stream(stream)))
 
+    def alloc_backward(self, device, with_params=True):
+        """Allocate contiguous per-group adjoint buffers (dL/du input, dL/du_hat and dL/dparams
+        outputs), bind them and return {problem index: dict(ids, gu, gh, gp)} (row j = instance
+        ids[j]); gp is None without parameter gradients."""
+        out = {}
+        per = [None] * self.n_inst
+        for pi, ids in self.groups().items():
+            p = self.problems[pi]
+            n = len(ids)
+            g = dict(ids=ids,
+                     gu=torch.zeros(n, p.n_vars, dtype=torch.float64, device=device),
+                     gh=torch.empty(n, p.n_vars, dtype=torch.float64, device=device),
+                     gp=(torch.empty(n, p.n_params, dtype=torch.float64, device=device)
+                         if with_params else None))
+            out[pi] = g
+            for j, i in enumerate(ids):
+                per[i] = (g["gu"][j], g["gh"][j], g["gp"][j] if with_params else None)
+        self.bind_backward(*[[x[k] for x in per] for k in range(3)])
+        return out
+
+    def bind_backward(self, grad_u, grad_u_hat, grad_params=None):
+        """Bind per-instance adjoint tensors (lists of length n_inst; grad_params may be None,
+        or hold None entries: no parameter gradient for those instances)."""
+        n = self.n_inst
+
+        def tab(ts):
+            return (C.c_void_p * max(n, 1))(*[(t.data_ptr() if t is not None else None)
+                                               for t in ts])
+
+        gp = tab(grad_params) if grad_params is not None else None
+        check(lib().snap_batch_bind_backward(self._h, tab(grad_u), tab(grad_u_hat), gp))
+        self._keep_bwd = (grad_u, grad_u_hat, grad_params)
+
+    def backward(self, stream=None):
+        """The adjoint of every instance in one persistent launch (after project)."""
+        ws = self.workspace(self._dev())
+        check(lib().snap_batch_project_backward(self._h, _ptr(ws), ws.numel(), _stream(stream)))
+
+    def backward_grouped(self, stream=None):
+        ws = self.workspace(self._dev())
+        check(lib().snap_batch_project_backward_grouped(self._h, _ptr(ws), ws.numel(),
+                                                        _stream(stream)))
+
+    def capture_graph_backward(self):
+        ws = self.workspace(self._dev())
+        check(lib().snap_batch_capture_graph_backward(self._h, _ptr(ws), ws.numel()))
+
+    def launch_graph_backward(self, stream=None):
+        check(lib().snap_batch_launch_graph_backward(self._h, _stream(stream)))
+
     def info(self):
         g, t, f = C.c_int(), C.c_int(), C.c_int()
         check(lib().snap_batch_info(self._h, C.byref(g), C.byref(t), C.byref(f)))

@@ -725,25 +725,10 @@ __global__ void k1d_backward_params(Geom1D g, int B, const double *__restrict__ 
   // launched as a programmatic dependent of the adjoint tile kernel: wait for its output
   asm volatile("griddepcontrol.wait;" ::: "memory");
   if (warp >= B) return;
-  double sm = 0.0, sex = 0.0, sfl = 0.0, sr = 0.0;
-  for (int k = 1 + lane; k < g.nt; k += 32) {
-    const BwdContrib c = contrib[(size_t)warp * g.nt + k];
-    sm += c.bm; sex += c.bex; sfl += c.bfl; sr += c.br;
-  }
-  sm = warp_sum(sm);
-  sex = warp_sum(sex);
-  sfl = warp_sum(sfl);
-  sr = warp_sum(sr);
   const bool bad = fst && fst[warp].status != SNAP_SAMPLE_OK;
-  const double *pg = params + (size_t)warp * g.n_params;
-  const double *g0 = gu + (size_t)warp * g.n_vars;     // slice 0 of dL/du
-  double *out = gp + (size_t)warp * g.n_params;
-  const SampleDerived dv = sd[warp];
-  for (int i = lane; i < g.nx; i += 32) {
-    const double v = g0[i] + g.dx * sm + 2.0 * g.dx * pg[i] * sex + 2.0 * dv.M * g.dx * sfl;
-    out[i] = bad ? NAN : v;
-  }
-  if (lane == 0) out[g.p_rate] = bad ? NAN : sr;
+  s1_param_grad<false>(g, gu + (size_t)warp * g.n_vars, params + (size_t)warp * g.n_params,
+                       sd[warp].M, contrib + (size_t)warp * g.nt, bad,
+                       gp + (size_t)warp * g.n_params, lane);
 }
 
 template <int NPL>

@@ -1,312 +1,67 @@
-// 1-D families A/B: implicit-function adjoint with the arithmetic spread over the SM's pipes.
-//
-// For every slice k >= 1 the adjoint solves K [a; b] = [gbar; 0] with the KKT matrix of
-// Appendix B at the solution (W = diag(w interior, wb at i in {0, h})):
-//     S b = J W^-1 gbar,   a = W^-1 (gbar - J^T b),   S = J W^-1 J^T.
-// J W^-1 gbar needs the interior sums sum gbar_i and sum u_i gbar_i (and, when the forward
-// factor is not cached, sum u_i and sum u_i^2 to rebuild S), so the kernel mirrors the forward:
-//   phase 1  (4 lanes per slice): float-pair split of u and gbar with integer operations only
-//            (|x - hi - lo| <= 2^-48 |x|), double-float sums;
-//   phase 2  (one slice per lane): S b = v in double-float, from the cached FP64 LDL^T factor
-//            or from S rebuilt in double-float; the per-slice contributions to dL/dtheta;
-//   phase 3  (4 lanes per slice): a_i = gbar_i / w - (dx b_m + 2 dx u_i b_e) / w with two
-//            FP64 FMAs per element.
-// The IC slices (a = 0) are written by the per-sample prepare kernel.  A slice whose values
-// leave the float-pair range is done by its owner lane in FP64.
+// 1-D families A/B: the per-problem implicit-function adjoint kernel, one warp per tile of 32
+// consecutive slices (bwd_tile, tile_1d_bwd.cuh, which also documents the three phases).  The
+// IC slices (a = 0) are written by the per-sample prepare kernel.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
 
 #include "slice_newton.cuh"
 #include "snap_internal.h"
+#include "tile_1d_bwd.cuh"
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
-
-__device__ __forceinline__ df64 shfl_df(df64 v, int off) {
-  return df64(__shfl_xor_sync(FULL, v.hi, off), __shfl_xor_sync(FULL, v.lo, off));
-}
-
-// error-free accumulation of h into (s, e): s + e tracks the running sum
-__device__ __forceinline__ void acc2(float &s, float &e, float h, float l) {
-  const float t = s + h, bb = t - s;
-  e += ((s - (t - bb)) + (h - bb)) + l;
-  s = t;
-}
-
-// (xh + xl)(yh + yl) accumulated into (s, e): TwoProd of the leading parts plus cross terms
-__device__ __forceinline__ void acc_prod(float &s, float &e, float xh, float xl, float yh, float yl) {
-  const float p = xh * yh;
-  float pe = fmaf(xh, yh, -p);
-  pe = fmaf(xh, yl, pe);
-  pe = fmaf(xl, yh, pe);
-  const float t = s + p, bb = t - s;
-  e += ((s - (t - bb)) + (p - bb)) + pe;
-  s = t;
-}
-
-__device__ __forceinline__ df64 df_pow_b(df64 x, int k) {
-  df64 r(1.0f, 0.0f);
-  while (k > 0) {
-    if (k & 1) r = r * x;
-    x = x * x;
-    k >>= 1;
+// Slices of one per-problem batch: slice s is slice s % nt of sample s / nt.
+struct DirectBwd {
+  long long total;
+  int nt, nx, n_rows, n_params;
+  const double *gu, *u, *lam;
+  const snap_stats *fst;
+  const SampleDerived *sd;
+  const SliceFactor *cache;
+  double *gh, *gp;
+  BwdContrib *contrib;
+  __device__ __forceinline__ int sample(long long s) const { return (int)(s / nt); }
+  __device__ __forceinline__ bool live(long long s) const { return s < total && (s % nt) != 0; }
+  __device__ __forceinline__ int slice_k(long long s) const { return (int)(s % nt); }
+  __device__ __forceinline__ const double *row_u(long long s) const { return u + (size_t)s * nx; }
+  __device__ __forceinline__ const double *row_g(long long s) const { return gu + (size_t)s * nx; }
+  __device__ __forceinline__ double *row_out(long long s) const { return gh + (size_t)s * nx; }
+  __device__ __forceinline__ const double *lam_of(long long s) const {
+    return lam + (size_t)sample(s) * n_rows;
   }
-  return r;
-}
-
-__device__ __forceinline__ df64 split_df(double x, bool &ok) {
-  float h, l;
-  ok &= df_split(x, h, l);
-  return df64(h, l);
-}
+  __device__ __forceinline__ bool bad(long long s) const {
+    return fst && fst[sample(s)].status != SNAP_SAMPLE_OK;
+  }
+  __device__ __forceinline__ SampleDerived derived(long long s) const { return sd[sample(s)]; }
+  __device__ __forceinline__ const SliceFactor *factor(long long s) const {
+    return cache ? cache + s : nullptr;
+  }
+  __device__ __forceinline__ BwdContrib *contrib_at(long long s) const { return contrib + s; }
+  __device__ __forceinline__ double *gp_of(long long s) const {
+    return gp ? gp + (size_t)sample(s) * n_params : nullptr;
+  }
+  // launched as a programmatic dependent of k1d_params: phase 1 overlaps it, the per-sample
+  // values and everything written after this point wait for its completion
+  __device__ __forceinline__ void before_solve(int) const {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+  }
+};
 
 __global__ void __launch_bounds__(128, 4)
 k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__restrict__ u,
-              const double *__restrict__ lam, const double *__restrict__ params,
-              const snap_stats *__restrict__ fst, const SampleDerived *__restrict__ sd,
-              const SliceFactor *__restrict__ cache, double *__restrict__ gh,
-              double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
-  const int lane = threadIdx.x & 31;
-  const int q = lane >> 2;
-  const int r = lane & 3;
+              const double *__restrict__ lam, const snap_stats *__restrict__ fst,
+              const SampleDerived *__restrict__ sd, const SliceFactor *__restrict__ cache,
+              double *__restrict__ gh, double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
   const long long total = (long long)B * g.nt;
   const long long ntiles = (total + 31) >> 5;
   const int wpb = blockDim.x >> 5;
-  const int nx = g.nx, ih = g.ih;
-  const bool need_s = cache == nullptr;
-  const df64 dxd(g.dx);
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  const DirectBwd ad{total, g.nt, g.nx, g.n_rows, g.n_params, gu, u, lam, fst, sd, cache,
+                     gh, gp, contrib};
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
-       tile += (long long)gridDim.x * wpb) {
-    const long long sbase = tile << 5;
-    // ---------------- phase 1: sums over the interior ----------------
-    df64 mg(0.0f, 0.0f), mug(0.0f, 0.0f), mu(0.0f, 0.0f), muu(0.0f, 0.0f);
-    int mok = 1;
-#pragma unroll 1
-    for (int rho = 0; rho < 4; ++rho) {
-      const long long s = sbase + 8 * rho + q;
-      float sg = 0.f, eg = 0.f, sug = 0.f, eug = 0.f, su = 0.f, eu = 0.f, suu = 0.f, euu = 0.f;
-      int ok = 1;
-      if (s < total && (s % g.nt) != 0) {
-        const double *urow = u + (size_t)s * nx;
-        const double *grow = gu + (size_t)s * nx;
-        constexpr int CH = 8;
-        for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
-          double2 vu[CH], vg[CH];
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
-            vu[c] = (i < nx) ? *reinterpret_cast<const double2 *>(urow + i) : make_double2(0.0, 0.0);
-            vg[c] = (i < nx) ? *reinterpret_cast<const double2 *>(grow + i) : make_double2(0.0, 0.0);
-          }
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
-            if (i >= nx) break;
-            float uh0, ul0, uh1, ul1, gh0, gl0, gh1, gl1;
-            ok &= df_split_trunc(vu[c].x, uh0, ul0);
-            ok &= df_split_trunc(vu[c].y, uh1, ul1);
-            ok &= df_split_trunc(vg[c].x, gh0, gl0);
-            ok &= df_split_trunc(vg[c].y, gh1, gl1);
-            if (i == 0 || i == ih) { uh0 = ul0 = gh0 = gl0 = 0.0f; }
-            if (i + 1 == ih) { uh1 = ul1 = gh1 = gl1 = 0.0f; }
-            acc2(sg, eg, gh0, gl0);
-            acc2(sg, eg, gh1, gl1);
-            acc_prod(sug, eug, uh0, ul0, gh0, gl0);
-            acc_prod(sug, eug, uh1, ul1, gh1, gl1);
-            if (need_s) {
-              acc2(su, eu, uh0, ul0);
-              acc2(su, eu, uh1, ul1);
-              acc_prod(suu, euu, uh0, ul0, uh0, ul0);
-              acc_prod(suu, euu, uh1, ul1, uh1, ul1);
-            }
-          }
-        }
-      }
-      df64 a_g = df_fast_two_sum(sg, eg), a_ug = df_fast_two_sum(sug, eug);
-      df64 a_u = df_fast_two_sum(su, eu), a_uu = df_fast_two_sum(suu, euu);
-#pragma unroll
-      for (int off = 1; off < 4; off <<= 1) {
-        a_g = a_g + shfl_df(a_g, off);
-        a_ug = a_ug + shfl_df(a_ug, off);
-        if (need_s) {
-          a_u = a_u + shfl_df(a_u, off);
-          a_uu = a_uu + shfl_df(a_uu, off);
-        }
-        ok &= __shfl_xor_sync(FULL, ok, off);
-      }
-      if (r == rho) { mg = a_g; mug = a_ug; mu = a_u; muu = a_uu; mok = ok; }
-    }
-    // ---------------- phase 2: one slice per lane ----------------
-    // launched as a programmatic dependent of k1d_params: phase 1 above overlaps it, the
-    // per-sample values and everything written below wait for its completion
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const long long s = sbase + 8 * r + q;
-    int live = 0;
-    double ciw = 0.0, ciwb = 0.0, ckx = 0.0, ck0 = 0.0, ckxb = 0.0, ck0b = 0.0;
-    if (s < total && (s % g.nt) != 0) {
-      live = 1;
-      const int b = (int)(s / g.nt);
-      const int k = (int)(s % g.nt);
-      const bool bad = fst && fst[b].status != SNAP_SAMPLE_OK;
-      const double *lb = lam + (size_t)b * g.n_rows;
-      const double *urow = u + (size_t)s * nx;
-      const double *grow = gu + (size_t)s * nx;
-      const double u0 = urow[0], uhv = urow[ih], g0 = grow[0], ghv = grow[ih];
-      const double lme = (g.rows & SL_ENERGY) ? lb[g.off_energy + k] : 0.0;
-      const double lbb = (g.rows & SL_BOUND) ? lb[g.off_bound + k] : 0.0;
-      bool ok = mok;
-      const df64 U0 = split_df(u0, ok), UH = split_df(uhv, ok), G0 = split_df(g0, ok), GH = split_df(ghv, ok);
-      const df64 LE = split_df(lme, ok), LB = split_df(lbb, ok);
-      const df64 two(2.0f, 0.0f), one(1.0f, 0.0f), zero(0.0f, 0.0f);
-      double bm = 0.0, be = 0.0, bbv = 0.0, w = 1.0, wb = 1.0;
-      if (ok) {
-        const df64 W = one + two * dxd * LE;
-        const df64 WB = W + two * LB;
-        const df64 iw = df64(1.0f, 0.0f) / W, iwb = df64(1.0f, 0.0f) / WB;
-        // v = J W^-1 gbar
-        const df64 pg2 = U0 * G0 + UH * GH;
-        const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
-        const df64 v0 = hm ? dxd * (mg * iw + (G0 + GH) * iwb) : zero;
-        const df64 v1 = he ? two * dxd * (mug * iw + pg2 * iwb) : zero;
-        const df64 v2 = hbnd ? two * pg2 * iwb : zero;
-        Ldl3<df64> f;
-        bool fok;
-        if (cache) {
-          const SliceFactor c = cache[s];
-          bool cok = true;
-          f.d0 = split_df(c.d0, cok); f.d1 = split_df(c.d1, cok); f.d2 = split_df(c.d2, cok);
-          f.l10 = split_df(c.l10, cok); f.l20 = split_df(c.l20, cok); f.l21 = split_df(c.l21, cok);
-          fok = cok && !(f.d0 == zero) && !(f.d1 == zero) && !(f.d2 == zero);
-          if (fok) {
-            f.i0 = one / f.d0; f.i1 = one / f.d1; f.i2 = one / f.d2;
-          }
-        } else {
-          SliceIn<df64> d;
-          d.dx = dxd;
-          d.n = df64((float)(nx - 2), 0.0f);
-          d.rows = g.rows;
-          d.nint = nx - 2;
-          SliceZ<df64> z;
-          z.p0 = U0; z.ph = UH;
-          df64 s00, s01, s02, s11, s12, s22;
-          slice_schur(d, z, mu, muu, iw, iwb, s00, s01, s02, s11, s12, s22);
-          fok = ldl3_factor(s00, s01, s02, s11, s12, s22, f);
-        }
-        if (fok) {
-          df64 xm, xe, xb;
-          ldl3_solve(f, v0, v1, v2, xm, xe, xb);
-          if (!hm) xm = zero;
-          if (!he) xe = zero;
-          if (!hbnd) xb = zero;
-          bm = (double)xm; be = (double)xe; bbv = (double)xb;
-          w = (double)W; wb = (double)WB;
-          // a = W^-1 (gbar - dx b_m - 2 dx u b_e [- 2 u b_b at the boundary])
-          const df64 kx = -(two * dxd * xe) * iw, k0 = -(dxd * xm) * iw;
-          const df64 kxb = -(two * dxd * xe + two * xb) * iwb, k0b = -(dxd * xm) * iwb;
-          ciw = (double)iw; ciwb = (double)iwb;
-          ckx = (double)kx; ck0 = (double)k0; ckxb = (double)kxb; ck0b = (double)k0b;
-        } else {
-          ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN;
-          bm = be = bbv = NAN;
-        }
-      } else {
-        // FP64 by this lane: sums, S and the solve
-        double sgd = 0.0, sugd = 0.0, sud = 0.0, suud = 0.0;
-        for (int i = 0; i < nx; ++i) {
-          if (i == 0 || i == ih) continue;
-          const double uv = urow[i], gv = grow[i];
-          sgd += gv;
-          sugd = fma(uv, gv, sugd);
-          sud += uv;
-          suud = fma(uv, uv, suud);
-        }
-        w = 1.0 + 2.0 * g.dx * lme;
-        wb = w + 2.0 * lbb;
-        const double iw = 1.0 / w, iwb = 1.0 / wb;
-        const double pg2 = u0 * g0 + uhv * ghv;
-        const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
-        const double v0 = hm ? g.dx * (sgd * iw + (g0 + ghv) * iwb) : 0.0;
-        const double v1 = he ? 2.0 * g.dx * (sugd * iw + pg2 * iwb) : 0.0;
-        const double v2 = hbnd ? 2.0 * pg2 * iwb : 0.0;
-        SliceIn<double> d;
-        d.dx = g.dx;
-        d.n = (double)(nx - 2);
-        d.rows = g.rows;
-        d.nint = nx - 2;
-        SliceZ<double> z;
-        z.p0 = u0; z.ph = uhv;
-        double s00, s01, s02, s11, s12, s22;
-        slice_schur(d, z, sud, suud, iw, iwb, s00, s01, s02, s11, s12, s22);
-        Ldl3<double> f;
-        if (ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-          ldl3_solve(f, v0, v1, v2, bm, be, bbv);
-          if (!hm) bm = 0.0;
-          if (!he) be = 0.0;
-          if (!hbnd) bbv = 0.0;
-        } else {
-          bm = be = bbv = NAN;
-        }
-        ciw = iw; ciwb = iwb;
-        ckx = -2.0 * g.dx * be * iw; ck0 = -g.dx * bm * iw;
-        ckxb = -(2.0 * g.dx * be + 2.0 * bbv) * iwb; ck0b = -g.dx * bm * iwb;
-      }
-      if (bad) { ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN; }
-      BwdContrib c{bm, 0.0, 0.0, 0.0};
-      if (g.rows & SL_ENERGY) {
-        const SampleDerived dv = sd[b];
-        const double t = (double)k / (double)(g.nt - 1);
-        const double ex = (double)df_pow_b(df64(dv.qh, dv.ql), k);
-        const bool expb = dv.E0 * ex >= dv.M * dv.M + g.energy_floor;
-        c.bex = expb ? be * ex : 0.0;
-        c.bfl = expb ? 0.0 : be;
-        c.br = expb ? -be * t * dv.E0 * ex : 0.0;
-      }
-      contrib[s] = c;
-      if (gp && (g.rows & SL_BOUND)) gp[(size_t)b * g.n_params + g.p_c + k] = bad ? NAN : bbv;
-      (void)w;
-      (void)wb;
-    }
-    // ---------------- phase 3: a = W^-1 (gbar - J^T b), 4 lanes per slice ----------------
-#pragma unroll 1
-    for (int rho = 0; rho < 4; ++rho) {
-      const int src = 4 * q + rho;
-      const double iw = __shfl_sync(FULL, ciw, src);
-      const double iwb = __shfl_sync(FULL, ciwb, src);
-      const double kx = __shfl_sync(FULL, ckx, src);
-      const double k0 = __shfl_sync(FULL, ck0, src);
-      const double kxb = __shfl_sync(FULL, ckxb, src);
-      const double k0b = __shfl_sync(FULL, ck0b, src);
-      const int lv = __shfl_sync(FULL, live, src);
-      const long long s2 = sbase + 8 * rho + q;
-      if (s2 >= total || !lv) continue;
-      const double *urow = u + (size_t)s2 * nx;
-      const double *grow = gu + (size_t)s2 * nx;
-      double *out = gh + (size_t)s2 * nx;
-      constexpr int CH = 8;
-      for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
-        double2 vu[CH], vg[CH];
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int i = i0 + 8 * c;
-          vu[c] = (i < nx) ? *reinterpret_cast<const double2 *>(urow + i) : make_double2(0.0, 0.0);
-          vg[c] = (i < nx) ? *reinterpret_cast<const double2 *>(grow + i) : make_double2(0.0, 0.0);
-        }
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          const int i = i0 + 8 * c;
-          if (i >= nx) break;
-          const bool b0 = (i == 0 || i == ih), b1 = (i + 1 == ih);
-          double2 w;
-          w.x = fma(vg[c].x, b0 ? iwb : iw, fma(vu[c].x, b0 ? kxb : kx, b0 ? k0b : k0));
-          w.y = fma(vg[c].y, b1 ? iwb : iw, fma(vu[c].y, b1 ? kxb : kx, b1 ? k0b : k0));
-          *reinterpret_cast<double2 *>(out + i) = w;
-        }
-      }
-    }
-  }
+       tile += (long long)gridDim.x * wpb)
+    bwd_tile(g, ad, tile << 5, cache == nullptr);
 }
 
 }  // namespace
@@ -328,6 +83,7 @@ void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const dou
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, params, stats, sd, cache,
+  (void)params;
+  cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, stats, sd, cache,
                      grad_u_hat, grad_params, contrib);
 }

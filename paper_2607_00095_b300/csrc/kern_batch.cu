@@ -30,6 +30,7 @@
 #include "sample_1d.cuh"
 #include "snap_internal.h"
 #include "tile_1d.cuh"
+#include "tile_1d_bwd.cuh"
 
 namespace {
 
@@ -280,6 +281,222 @@ __global__ void __launch_bounds__(kThreads, 2) k_batch(BatchArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Adjoint of an uneven batch: the same work lists and queues as the forward, the per-family
+// adjoint device code (bwd_tile for 1-D tiles, frame2d_backward for 2-D frames), per-slice /
+// per-frame contributions to dL/dparams in the statistics area of the workspace, and the
+// per-instance parameter gradient formed by the last unit of the instance to finish.
+// ---------------------------------------------------------------------------------------
+struct BwdRec {
+  const double *gu;        // dL/du (input)
+  double *gh, *gp;         // dL/du_hat, dL/dparams (outputs; gp may be null)
+};
+
+struct BwdArgs {
+  const InstRec *inst;
+  const BwdRec *bwd;
+  const GroupRec *groups;
+  const int *list;
+  const Item1D *items1d;
+  const Item2D *items2d;
+  int n1d, n2d, order;
+  Hdr *hdr;
+  unsigned int *done;
+  BwdContrib *contrib;
+};
+
+// Address policy of a 1-D adjoint tile of a group (the slices of instance i of the group are
+// i nt .. i nt + nt - 1 of the group's virtual batch; the tile is [s0, s1)).
+struct BatchBwdTiles {
+  const InstRec *inst;
+  const BwdRec *bwd;
+  const int *list;
+  BwdContrib *contrib;                   // the group's first contribution
+  SampleDerived *sdw;                    // this warp's table
+  const TileCtx *c;
+  long long s0, s1;
+  __device__ __forceinline__ int nt() const { return c->nt; }
+  __device__ __forceinline__ int inst_of(long long s) const { return (int)s / nt(); }
+  __device__ __forceinline__ int id_of(long long s) const { return list[c->list_off + inst_of(s)]; }
+  __device__ __forceinline__ bool live(long long s) const {
+    return s < s1 && ((int)s % nt()) != 0;
+  }
+  __device__ __forceinline__ int slice_k(long long s) const { return (int)s % nt(); }
+  __device__ __forceinline__ const double *row_u(long long s) const {
+    return inst[id_of(s)].u + (size_t)slice_k(s) * c->nx;
+  }
+  __device__ __forceinline__ const double *row_g(long long s) const {
+    return bwd[id_of(s)].gu + (size_t)slice_k(s) * c->nx;
+  }
+  __device__ __forceinline__ double *row_out(long long s) const {
+    return bwd[id_of(s)].gh + (size_t)slice_k(s) * c->nx;
+  }
+  __device__ __forceinline__ const double *lam_of(long long s) const { return inst[id_of(s)].lam; }
+  __device__ __forceinline__ bool bad(long long s) const {
+    return inst[id_of(s)].stats->status != SNAP_SAMPLE_OK;
+  }
+  __device__ __forceinline__ SampleDerived derived(long long s) const {
+    return sdw[inst_of(s) - c->first_inst];
+  }
+  __device__ __forceinline__ const SliceFactor *factor(long long) const { return nullptr; }
+  __device__ __forceinline__ BwdContrib *contrib_at(long long s) const { return contrib + (int)s; }
+  __device__ __forceinline__ double *gp_of(long long s) const { return bwd[id_of(s)].gp; }
+  // the tile's instances: derived values into the warp's table; the IC block of an instance
+  // whose slice 0 is in the tile (a = 0 there, and the boundary parameter of slice 0)
+  __device__ __forceinline__ void before_solve(int lane) const {
+    const int n = nt(), a0 = (int)s0, a1 = (int)s1;
+    for (int i = a0 / n; i * n < a1; ++i) {
+      const int id = list[c->list_off + i];
+      const InstRec &R = inst[id];
+      const SampleDerived d = s1_derive(c->g, R.params, lane);
+      if (lane == 0) sdw[i - c->first_inst] = d;
+      if (i * n >= a0) {
+        const BwdRec &W = bwd[id];
+        const bool bd = R.stats->status != SNAP_SAMPLE_OK;
+        for (int x = lane; x < c->nx; x += 32) W.gh[x] = bd ? NAN : 0.0;
+        if (lane == 0 && W.gp && (c->g.rows & SL_BOUND)) W.gp[c->g.p_c] = bd ? NAN : 0.0;
+      }
+    }
+    __syncwarp();
+  }
+};
+
+template <int M>
+__device__ __forceinline__ void run_frame_bwd(unsigned char *smem, const GroupRec &G,
+                                              const InstRec &R, const BwdRec &W, int f,
+                                              BwdContrib *out) {
+  constexpr int NN = 4 * M * M;
+  View2D<M> v(smem);
+  const bool bd = R.stats->status != SNAP_SAMPLE_OK;
+  frame2d_backward<M>(v, W.gu + (size_t)f * 2 * NN, R.u + (size_t)f * 2 * NN,
+                      R.lam[(size_t)G.nt * NN + f], R.params, f, G.nt, bd, G.Q, G.I,
+                      W.gh + (size_t)f * 2 * NN, out);
+}
+
+__device__ __forceinline__ void batch_2d_bwd(const BwdArgs &a, unsigned char *smem) {
+  __shared__ int s_item, s_last;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(&a.hdr->q2d, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n2d) break;
+    const Item2D w = a.items2d[it];
+    const GroupRec &G = a.groups[w.group];
+    const int il = w.unit / G.nt, f = w.unit % G.nt;
+    const int id = a.list[G.list_off + il];
+    const InstRec &R = a.inst[id];
+    const BwdRec &W = a.bwd[id];
+    BwdContrib *cs = a.contrib + G.bst_off + w.unit;
+    switch (G.M) {
+      case 2: run_frame_bwd<2>(smem, G, R, W, f, cs); break;
+      case 4: run_frame_bwd<4>(smem, G, R, W, f, cs); break;
+      case 8: run_frame_bwd<8>(smem, G, R, W, f, cs); break;
+      case 16: run_frame_bwd<16>(smem, G, R, W, f, cs); break;
+      default: run_frame_bwd<32>(smem, G, R, W, f, cs); break;
+    }
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned old = atomicAdd(&a.done[id], 1u);
+      s_last = (old + 1u == (unsigned)G.nt);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x < 32 && W.gp) {
+      __threadfence();
+      frame2d_param_grad<true>(a.contrib + G.bst_off + (long long)il * G.nt, G.nt,
+                               R.stats->status != SNAP_SAMPLE_OK, W.gp, threadIdx.x);
+    }
+    __syncthreads();
+  }
+}
+
+// Arrival of adjoint tile `it`: count its slices per instance; the last arrival forms the
+// instance's dL/dparams.
+__device__ __noinline__ void finish_tile_bwd(const BwdArgs &a, unsigned it, int lane,
+                                             const SampleDerived *sdw, int first_inst) {
+  const Item1D w = a.items1d[it];
+  const GroupRec &G = a.groups[w.group];
+  const int nt = G.nt;
+  const int s0 = w.s0, s1 = w.s1;
+  for (int i = s0 / nt; i * nt < s1; ++i) {
+    const int a0 = (i * nt > s0) ? i * nt : s0;
+    const int b0 = ((i + 1) * nt < s1) ? (i + 1) * nt : s1;
+    const int id = a.list[G.list_off + i];
+    unsigned last = 0;
+    if (lane == 0) {
+      const unsigned cnt = (unsigned)(b0 - a0);
+      last = (atomicAdd(&a.done[id], cnt) + cnt == (unsigned)nt) ? 1u : 0u;
+    }
+    last = __shfl_sync(0xffffffffu, last, 0);
+    const BwdRec &W = a.bwd[id];
+    if (last && W.gp) {
+      __threadfence();
+      const InstRec &R = a.inst[id];
+      s1_param_grad<true>(G.g, W.gu, R.params, sdw[i - first_inst].M,
+                          a.contrib + G.bst_off + (long long)i * nt,
+                          R.stats->status != SNAP_SAMPLE_OK, W.gp, lane);
+    }
+  }
+}
+
+__device__ __forceinline__ void batch_1d_bwd(const BwdArgs &a, SampleDerived *sdw, TileCtx *cx) {
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    unsigned it = 0;
+    if (lane == 0) it = atomicAdd(&a.hdr->q1d, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (unsigned)a.n1d) break;
+    const Item1D w = a.items1d[it];
+    const GroupRec &G = a.groups[w.group];
+    const int nt = G.nt;
+    const int i0 = w.s0 / nt;
+    {
+      const int *src = reinterpret_cast<const int *>(&G.g);
+      int *dst = reinterpret_cast<int *>(&cx->g);
+      if (lane < (int)(sizeof(Geom1D) / sizeof(int))) dst[lane] = src[lane];
+    }
+    if (lane == 0) {
+      cx->nt = nt;
+      cx->nx = G.g.nx;
+      cx->list_off = G.list_off;
+      cx->first_inst = i0;
+    }
+    __syncwarp();
+    BatchBwdTiles ad;
+    ad.inst = a.inst;
+    ad.bwd = a.bwd;
+    ad.list = a.list;
+    ad.contrib = a.contrib + G.bst_off;
+    ad.sdw = sdw;
+    ad.c = cx;
+    ad.s0 = w.s0;
+    ad.s1 = w.s1;
+    bwd_tile(cx->g, ad, w.s0, true);
+    // arrival: every lane's contributions and outputs are fenced before lane 0 counts
+    __threadfence();
+    __syncwarp();
+    finish_tile_bwd(a, it, lane, sdw, i0);
+    __syncwarp();                        // the context is rewritten by the next tile
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_batch_bwd(BwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_batch_bwd[];
+  __shared__ SampleDerived sdtab[kWarps][kMaxTileInst];
+  __shared__ TileCtx ctx[kWarps];
+  SampleDerived *sdw = sdtab[threadIdx.x >> 5];
+  TileCtx *cx = &ctx[threadIdx.x >> 5];
+  if (a.order == 0) {
+    if (a.n2d > 0) batch_2d_bwd(a, smem_batch_bwd);
+    if (a.n1d > 0) batch_1d_bwd(a, sdw, cx);
+  } else {
+    if (a.n1d > 0) batch_1d_bwd(a, sdw, cx);
+    if (a.n2d > 0) {
+      __syncthreads();
+      batch_2d_bwd(a, smem_batch_bwd);
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -314,6 +531,13 @@ struct snap_batch {
   Item2D *d_items2d = nullptr;
   size_t cap1d = 0, cap2d = 0;
   cudaGraphExec_t graph = nullptr;
+  // adjoint
+  BwdRec *d_bwd = nullptr;
+  std::vector<BwdRec> h_bwd;
+  std::vector<char> group_contig_bwd;
+  bool bound_bwd = false;
+  int grid_bwd = 0;                      // persistent grid of the adjoint kernel
+  cudaGraphExec_t graph_bwd = nullptr;
 };
 
 namespace {
@@ -365,10 +589,11 @@ void build_items(const snap_batch *b, const snap_batch_schedule &s, std::vector<
   }
 }
 
-int grid_blocks(const snap_batch *b, int ctas_per_sm) {
+template <class K>
+int grid_blocks_of(const snap_batch *b, int ctas_per_sm, K kernel) {
   int sms = 148, occ = 1;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch, kThreads, b->smem_bytes) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kThreads, b->smem_bytes) !=
           cudaSuccess ||
       occ < 1)
     occ = 1;
@@ -376,6 +601,8 @@ int grid_blocks(const snap_batch *b, int ctas_per_sm) {
   if (per > occ) per = occ;
   return sms * per;
 }
+
+int grid_blocks(const snap_batch *b, int ctas_per_sm) { return grid_blocks_of(b, ctas_per_sm, k_batch); }
 
 snap_status upload_items(snap_batch *b) {
   std::vector<Item1D> i1;
@@ -392,11 +619,14 @@ snap_status upload_items(snap_batch *b) {
   b->n1d = (int)i1.size();
   b->n2d = (int)i2.size();
   b->grid = grid_blocks(b, b->sched.ctas_per_sm);
+  b->grid_bwd = grid_blocks_of(b, b->sched.ctas_per_sm, k_batch_bwd);
   return SNAP_OK;
 }
 
 void free_batch(snap_batch *b) {
   if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->graph_bwd) cudaGraphExecDestroy(b->graph_bwd);
+  cudaFree(b->d_bwd);
   cudaFree(b->d_inst);
   cudaFree(b->d_groups);
   cudaFree(b->d_list);
@@ -453,6 +683,37 @@ snap_status launch_batch(snap_batch *b, const snap_options &o, unsigned long lon
   cudaError_t e = cudaMemsetAsync(ws, 0, hdr_bytes(b), s);
   if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   k_batch<<<b->grid, kThreads, b->smem_bytes, s>>>(a);
+  snap_note_launch(1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
+  return SNAP_OK;
+}
+
+snap_status launch_batch_bwd(snap_batch *b, void *ws, size_t bytes, cudaStream_t s) {
+  if (!b->bound || !b->bound_bwd)
+    return snap_fail_msg(SNAP_ERR_NOT_READY, "batch adjoint used before snap_batch_bind(_backward)");
+  if (b->n_inst == 0) return SNAP_OK;
+  if (!ws || bytes < batch_ws_bytes(b) || !aligned(ws, 256))
+    return snap_fail_msg(SNAP_ERR_WORKSPACE, "batch workspace missing, unaligned or too small");
+  char *c = (char *)ws;
+  BwdArgs a;
+  a.inst = b->d_inst;
+  a.bwd = b->d_bwd;
+  a.groups = b->d_groups;
+  a.list = b->d_list;
+  a.items1d = b->d_items1d;
+  a.items2d = b->d_items2d;
+  a.n1d = b->n1d;
+  a.n2d = b->n2d;
+  a.order = b->sched.order;
+  a.hdr = (Hdr *)c;
+  a.done = (unsigned int *)(c + sizeof(Hdr));
+  // per-slice / per-frame contributions in the statistics area (32 of its 40 bytes a record)
+  a.contrib = (BwdContrib *)(c + hdr_bytes(b));
+  static_assert(sizeof(BwdContrib) <= sizeof(BlockStat), "contributions fit the statistics area");
+  cudaError_t e = cudaMemsetAsync(ws, 0, hdr_bytes(b), s);
+  if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
+  k_batch_bwd<<<b->grid_bwd, kThreads, b->smem_bytes, s>>>(a);
   snap_note_launch(1);
   e = cudaGetLastError();
   if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
@@ -555,6 +816,7 @@ SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *pro
   ok = ok && cudaMalloc(&b->d_list, sizeof(int) * std::max<size_t>(b->list.size(), 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_items1d, sizeof(Item1D) * std::max<size_t>(b->cap1d, 1)) == cudaSuccess;
   ok = ok && cudaMalloc(&b->d_items2d, sizeof(Item2D) * std::max<size_t>(b->cap2d, 1)) == cudaSuccess;
+  ok = ok && cudaMalloc(&b->d_bwd, sizeof(BwdRec) * std::max(n_inst, 1)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     free_batch(b);
@@ -568,8 +830,10 @@ SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *pro
     return snap_fail_msg(SNAP_ERR_CUDA, "upload of the batch tables failed");
   }
   if (b->smem_bytes > 0 &&
-      cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)b->smem_bytes) != cudaSuccess) {
+      (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)b->smem_bytes) != cudaSuccess ||
+       cudaFuncSetAttribute(k_batch_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)b->smem_bytes) != cudaSuccess)) {
     free_batch(b);
     return snap_fail_msg(SNAP_ERR_CUDA, "shared-memory size of the batch kernel refused");
   }
@@ -780,6 +1044,120 @@ SNAP_API snap_status snap_batch_launch_graph(snap_batch_t b, snap_stream_t strea
   if (b->n_inst == 0) return SNAP_OK;
   if (!b->graph) return snap_fail_msg(SNAP_ERR_NOT_READY, "no graph captured");
   const cudaError_t e = cudaGraphLaunch(b->graph, (cudaStream_t)stream);
+  if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
+  snap_note_launch(1);
+  return SNAP_OK;
+}
+
+SNAP_API snap_status snap_batch_bind_backward(snap_batch_t b, const double *const *grad_u,
+                                              double *const *grad_u_hat,
+                                              double *const *grad_params) {
+  if (!b) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null batch");
+  if (b->n_inst > 0 && (!grad_u || !grad_u_hat))
+    return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null pointer table");
+  std::vector<BwdRec> rec(b->n_inst);
+  char msg[128];
+  for (int i = 0; i < b->n_inst; ++i) {
+    const snap_problem *p = b->probs[b->inst_problem[i]];
+    const unsigned va = p->desc.family != SNAP_FAMILY_C_DIV_ENERGY ? 16u : 8u;
+    double *gp = grad_params ? grad_params[i] : nullptr;
+    if (!grad_u[i] || !grad_u_hat[i] || !aligned(grad_u[i], va) || !aligned(grad_u_hat[i], va) ||
+        (gp && !aligned(gp, 8))) {
+      snprintf(msg, sizeof(msg), "instance %d: null or misaligned adjoint buffer", i);
+      return snap_fail_msg(SNAP_ERR_INVALID_ARG, msg);
+    }
+    rec[i] = BwdRec{grad_u[i], grad_u_hat[i], gp};
+  }
+  if (b->n_inst > 0 &&
+      cudaMemcpy(b->d_bwd, rec.data(), sizeof(BwdRec) * rec.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return snap_fail_msg(SNAP_ERR_CUDA, "upload of the adjoint pointer table failed");
+  b->group_contig_bwd.assign(b->groups.size(), 1);
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    const snap_problem *p = b->probs[b->group_problem[k]];
+    const auto &ids = b->group_inst[k];
+    for (size_t j = 1; j < ids.size(); ++j) {
+      const BwdRec &x = rec[ids[j - 1]], &y = rec[ids[j]];
+      if (y.gu != x.gu + p->info.n_vars || y.gh != x.gh + p->info.n_vars ||
+          (x.gp == nullptr) != (y.gp == nullptr) || (x.gp && y.gp != x.gp + p->info.n_params))
+        b->group_contig_bwd[k] = 0;
+    }
+  }
+  b->h_bwd = rec;
+  b->bound_bwd = true;
+  return SNAP_OK;
+}
+
+SNAP_API snap_status snap_batch_project_backward(snap_batch_t b, void *workspace,
+                                                 size_t workspace_bytes, snap_stream_t stream) {
+  if (!b) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null batch");
+  return launch_batch_bwd(b, workspace, workspace_bytes, (cudaStream_t)stream);
+}
+
+SNAP_API snap_status snap_batch_project_backward_grouped(snap_batch_t b, void *workspace,
+                                                         size_t workspace_bytes,
+                                                         snap_stream_t stream) {
+  if (!b) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null batch");
+  if (!b->bound || !b->bound_bwd)
+    return snap_fail_msg(SNAP_ERR_NOT_READY, "batch adjoint used before snap_batch_bind(_backward)");
+  if (b->n_inst == 0) return SNAP_OK;
+  if (!workspace || workspace_bytes < batch_ws_bytes(b) || !aligned(workspace, 256))
+    return snap_fail_msg(SNAP_ERR_WORKSPACE, "batch workspace missing, unaligned or too small");
+  for (size_t k = 0; k < b->groups.size(); ++k)
+    if (!b->group_contig[k] || !b->group_contig_bwd[k])
+      return snap_fail_msg(SNAP_ERR_UNSUPPORTED,
+                           "grouped launches need each group's buffers contiguous");
+  for (size_t k = 0; k < b->groups.size(); ++k) {
+    const snap_problem *p = b->probs[b->group_problem[k]];
+    const int id0 = b->group_inst[k][0];
+    const InstRec &r = b->h_inst[id0];
+    const BwdRec &w = b->h_bwd[id0];
+    const int n = (int)b->group_inst[k].size();
+    cudaError_t e;
+    if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
+      e = launch_2d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, nullptr, w.gh, w.gp,
+                             workspace, (cudaStream_t)stream);
+    else
+      e = launch_1d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, nullptr, w.gh, w.gp,
+                             workspace, (cudaStream_t)stream);
+    if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
+  }
+  return SNAP_OK;
+}
+
+SNAP_API snap_status snap_batch_capture_graph_backward(snap_batch_t b, void *workspace,
+                                                       size_t workspace_bytes) {
+  if (!b) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null batch");
+  if (!b->bound || !b->bound_bwd)
+    return snap_fail_msg(SNAP_ERR_NOT_READY, "batch adjoint used before snap_batch_bind(_backward)");
+  cudaStream_t s;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+    return snap_fail_msg(SNAP_ERR_CUDA, "stream create");
+  cudaGraph_t g = nullptr;
+  snap_status st = SNAP_OK;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    st = snap_fail_msg(SNAP_ERR_CUDA, "begin capture");
+  } else {
+    st = launch_batch_bwd(b, workspace, workspace_bytes, s);
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st == SNAP_OK && e != cudaSuccess) st = snap_fail_msg(SNAP_ERR_CUDA, "end capture");
+  }
+  cudaGraphExec_t x = nullptr;
+  if (st == SNAP_OK && g && cudaGraphInstantiate(&x, g, 0) != cudaSuccess)
+    st = snap_fail_msg(SNAP_ERR_CUDA, "graph instantiate");
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(s);
+  if (st != SNAP_OK) return st;
+  if (b->graph_bwd) cudaGraphExecDestroy(b->graph_bwd);
+  b->graph_bwd = x;
+  return SNAP_OK;
+}
+
+SNAP_API snap_status snap_batch_launch_graph_backward(snap_batch_t b, snap_stream_t stream) {
+  if (!b) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null batch");
+  if (b->n_inst == 0) return SNAP_OK;
+  if (!b->graph_bwd) return snap_fail_msg(SNAP_ERR_NOT_READY, "no adjoint graph captured");
+  const cudaError_t e = cudaGraphLaunch(b->graph_bwd, (cudaStream_t)stream);
   if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   snap_note_launch(1);
   return SNAP_OK;

@@ -163,4 +163,37 @@ __device__ __forceinline__ void s1_finalize(const BlockStat *__restrict__ bs, in
   }
 }
 
+// dL/dparams of one sample (one warp; fixed order, so the bits do not depend on which warp
+// runs it) from the per-slice contributions c[1..nt) of its adjoint: the IC block passes
+// dL/du of slice 0 (g0) to dL/dg, the mass / energy rows add dx b_m, 2 dx g b_e (exponential
+// branch) and 2 M dx b_fl (floor branch) to every g_i, and the rate receives sum b_r.  M is the
+// sample's dx sum g.  kCoherent reads the contributions through L2 only (written by other
+// warps of a running kernel).
+template <bool kCoherent>
+__device__ __forceinline__ void s1_param_grad(const Geom1D &g, const double *__restrict__ g0,
+                                              const double *__restrict__ pg, double M,
+                                              const BwdContrib *__restrict__ c, bool bad,
+                                              double *__restrict__ out, int lane) {
+  double sm = 0.0, sex = 0.0, sfl = 0.0, sr = 0.0;
+  for (int k = 1 + lane; k < g.nt; k += 32) {
+    if (kCoherent) {
+      const double2 a = __ldcg(reinterpret_cast<const double2 *>(c + k));
+      const double2 b = __ldcg(reinterpret_cast<const double2 *>(c + k) + 1);
+      sm += a.x; sex += a.y; sfl += b.x; sr += b.y;
+    } else {
+      const BwdContrib q = c[k];
+      sm += q.bm; sex += q.bex; sfl += q.bfl; sr += q.br;
+    }
+  }
+  sm = s1_warp_sum(sm);
+  sex = s1_warp_sum(sex);
+  sfl = s1_warp_sum(sfl);
+  sr = s1_warp_sum(sr);
+  for (int i = lane; i < g.nx; i += 32) {
+    const double v = g0[i] + g.dx * sm + 2.0 * g.dx * pg[i] * sex + 2.0 * M * g.dx * sfl;
+    out[i] = bad ? NAN : v;
+  }
+  if (lane == 0) out[g.p_rate] = bad ? NAN : sr;
+}
+
 }  // namespace
