@@ -256,9 +256,6 @@ SNAP_API snap_status snap_problem_active_rows(snap_problem_t p, unsigned char *a
  * snap_constraint_residual share one requirement). */
 SNAP_API snap_status snap_workspace_size(snap_problem_t p, int B, size_t *bytes);
 
-/* Bytes of the optional adjoint cache written by snap_project (per-block factor data). */
-SNAP_API snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes);
-
 /* Forward projection of B samples (eq. (2) solved by the Newton-KKT iteration of
  * Appendix B with an Armijo line search on phi = 1/2 ||F||^2 and per-block convergence
  * masks).
@@ -268,8 +265,6 @@ SNAP_API snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *by
  *   u       [B][n_vars]    projected samples (device, written; may not alias inputs)
  *   lambda  [B][n_rows_nominal] multipliers, sign of L = f + lambda^T h (device, written)
  *   stats   [B]            per-sample statistics (device, written) or NULL
- *   adjoint_cache          NULL, or snap_adjoint_cache_size bytes (device, written) that
- *                          snap_project_backward can reuse instead of refactoring
  *   opt                    NULL for defaults (host)
  *   workspace              snap_workspace_size(p, B) bytes of device scratch
  * Errors: INVALID_ARG (B < 0, B > max_batch, null required pointer, bad options),
@@ -277,26 +272,27 @@ SNAP_API snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *by
  * B = 0 is a no-op. */
 SNAP_API snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const double *params,
                          const double *u0, double *u, double *lambda, snap_stats *stats,
-                         void *adjoint_cache, const snap_options *opt, void *workspace,
-                         size_t workspace_bytes, snap_stream_t stream);
+                         const snap_options *opt, void *workspace, size_t workspace_bytes,
+                         snap_stream_t stream);
 
 /* Backward pass of the projection by the implicit-function theorem on
  * F(u, lambda; u_hat, theta) = 0 (Appendix B system at the solution, no inertia shift):
  *     K [a ; b] = [grad_u ; 0],  dL/du_hat = a,  dL/dtheta = -b^T dh/dtheta.
+ * The per-block factors of K are rebuilt from (u, lambda): storing them in the forward pass and
+ * reading them back measured slower than rebuilding them.
  *   grad_u      [B][n_vars]    upstream gradient dL/du (device, read)
  *   u, lambda   forward outputs (device, read)
  *   params      forward parameters (device, read)
  *   stats       forward stats (device) or NULL; samples whose status is not OK get NaN
- *   adjoint_cache  the cache snap_project wrote, or NULL to recompute the factors from u
  *   grad_u_hat  [B][n_vars]    (device, written)
  *   grad_params [B][n_params]  (device, written) or NULL; layout of params
  *   workspace   snap_workspace_size(p, B) bytes
  * Errors as snap_project. */
 SNAP_API snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
                                   const double *u, const double *lambda, const double *params,
-                                  const snap_stats *stats, const void *adjoint_cache,
-                                  double *grad_u_hat, double *grad_params, void *workspace,
-                                  size_t workspace_bytes, snap_stream_t stream);
+                                  const snap_stats *stats, double *grad_u_hat,
+                                  double *grad_params, void *workspace, size_t workspace_bytes,
+                                  snap_stream_t stream);
 
 /* Constraint residual h(u; theta) of every nominal row (the per-type constraint error of
  * the Additional Results section is computed from it).
@@ -342,7 +338,7 @@ SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, doub
  * counterpart; this entry point exists for callers that cannot allocate device memory where
  * they project (a host callback or plugin where cudaMalloc is not permitted, or an embedding
  * with no allocator of its own that cannot size a workspace per batch).  The caller still
- * passes all inputs and outputs, with the meaning and layout of snap_project; no adjoint cache.
+ * passes all inputs and outputs, with the meaning and layout of snap_project.
  *   - It calls no cudaMalloc / cudaFree or any other allocating routine.
  *   - Limit: snap_workspace_size(p, B) must not exceed SNAP_NOALLOC_SCRATCH_BYTES (about
  *     80 bytes per time slice plus 64 per sample: e.g. B * nt <= 100,000 slices); larger

@@ -62,10 +62,9 @@ _PROTOS = {
     "snap_problem_pattern": (C.c_int, [_vp, _ip, _ip]),
     "snap_problem_active_rows": (C.c_int, [_vp, C.POINTER(C.c_uint8)]),
     "snap_workspace_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
-    "snap_adjoint_cache_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),
-    "snap_project": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+    "snap_project": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp,
                                C.POINTER(Options), _vp, C.c_size_t, _vp]),
-    "snap_project_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+    "snap_project_backward": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                         _vp, C.c_size_t, _vp]),
     "snap_constraint_residual": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp, C.c_size_t, _vp]),
     "snap_pcfm_workspace_size": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_size_t)]),

@@ -86,11 +86,6 @@ class Problem:
         check(lib().snap_workspace_size(self._h, B, C.byref(n)))
         return n.value
 
-    def cache_bytes(self, B):
-        n = C.c_size_t()
-        check(lib().snap_adjoint_cache_size(self._h, B, C.byref(n)))
-        return n.value
-
     def workspace(self, B, device):
         key = (B, str(device))
         ws = self._ws.get(key)
@@ -131,9 +126,8 @@ class Problem:
                 raise ValueError(f"{name} holds {t.numel()} elements; this problem needs {n} "
                                  f"for B = {B}")
 
-    def project(self, u_hat, params, u0=None, opts=None, cache=False, out=None, stream=None,
-                workspace=None):
-        """Returns (u [B, n_vars], lambda [B, n_rows], stats uint8 [B, 40], cache or None)."""
+    def project(self, u_hat, params, u0=None, opts=None, out=None, stream=None, workspace=None):
+        """Returns (u [B, n_vars], lambda [B, n_rows], stats uint8 [B, 40])."""
         B = u_hat.shape[0]
         u_hat = u_hat.reshape(B, self.n_vars)
         self._check_dev(u_hat, params, u0)
@@ -146,16 +140,13 @@ class Problem:
             u, lam, st = out
             self._check_dev(u, lam)
         self._check_sizes(B, u_hat, params, u, lam, st)
-        cb = None
-        if cache:
-            cb = torch.empty(max(self.cache_bytes(B), 8), dtype=torch.uint8, device=dev)
         ws = workspace if workspace is not None else self.workspace(B, dev)
         o = opts if opts is not None else options()
         check(lib().snap_project(self._h, B, _ptr(u_hat), _ptr(params),
                                  _ptr(u0.reshape(B, self.n_vars)) if u0 is not None else None,
-                                 _ptr(u), _ptr(lam), _ptr(st), _ptr(cb), C.byref(o), _ptr(ws),
+                                 _ptr(u), _ptr(lam), _ptr(st), C.byref(o), _ptr(ws),
                                  ws.numel(), _stream(stream)))
-        return u, lam, st, cb
+        return u, lam, st
 
     def project_noalloc(self, u_hat, params, u, lam, st, opts=None, stream=None):
         """snap_project_noalloc: the 1-D forward projection into caller-given outputs, with the
@@ -200,8 +191,7 @@ class Problem:
                                      C.byref(o), _ptr(ws), ws.numel(), _stream(stream)))
         return u, lam, st
 
-    def backward(self, grad_u, u, lam, params, stats=None, cache=None, stream=None,
-                 with_params=True):
+    def backward(self, grad_u, u, lam, params, stats=None, stream=None, with_params=True):
         B = u.shape[0]
         grad_u = grad_u.reshape(B, self.n_vars).contiguous()
         self._check_dev(grad_u, u, lam, params)
@@ -209,7 +199,7 @@ class Problem:
         gp = torch.empty(B, self.n_params, dtype=torch.float64, device=u.device) if with_params else None
         ws = self.workspace(B, u.device)
         check(lib().snap_project_backward(self._h, B, _ptr(grad_u), _ptr(u), _ptr(lam),
-                                          _ptr(params), _ptr(stats), _ptr(cache), _ptr(gh),
+                                          _ptr(params), _ptr(stats), _ptr(gh),
                                           _ptr(gp), _ptr(ws), ws.numel(), _stream(stream)))
         return gh, gp
 
@@ -239,34 +229,23 @@ def vorticity_problem(N, nt, max_batch=0):
 
 
 class SnapProject(torch.autograd.Function):
-    """u = projection(u_hat; params) with the implicit-function adjoint as backward.
-
-    store_factor: True keeps the per-block factors from the forward pass for the backward,
-    False recomputes them from (u, lambda), "auto" stores them when they take less than a
-    quarter of the free device memory.
-    """
+    """u = projection(u_hat; params) with the implicit-function adjoint as backward (the
+    per-block factors are rebuilt from (u, lambda) in the backward pass)."""
 
     @staticmethod
-    def forward(ctx, u_hat, params, problem, store_factor="auto", opts=None):
-        B = u_hat.shape[0]
-        store = store_factor
-        if store == "auto":
-            free, _ = torch.cuda.mem_get_info(u_hat.device)
-            store = problem.cache_bytes(B) < 0.25 * free
-        u, lam, st, cb = problem.project(u_hat.detach().contiguous(), params.detach().contiguous(),
-                                         opts=opts, cache=bool(store))
+    def forward(ctx, u_hat, params, problem, opts=None):
+        u, lam, st = problem.project(u_hat.detach().contiguous(), params.detach().contiguous(),
+                                     opts=opts)
         ctx.problem = problem
-        ctx.save_for_backward(u, lam, params.detach(), st, cb if cb is not None else torch.empty(0))
-        ctx.has_cache = cb is not None
+        ctx.save_for_backward(u, lam, params.detach(), st)
         ctx.shape = u_hat.shape
         return u.reshape(u_hat.shape)
 
     @staticmethod
     def backward(ctx, grad_u):
-        u, lam, params, st, cb = ctx.saved_tensors
-        gh, gp = ctx.problem.backward(grad_u.contiguous(), u, lam, params.contiguous(), stats=st,
-                                      cache=cb if ctx.has_cache else None)
-        return gh.reshape(ctx.shape), gp, None, None, None
+        u, lam, params, st = ctx.saved_tensors
+        gh, gp = ctx.problem.backward(grad_u.contiguous(), u, lam, params.contiguous(), stats=st)
+        return gh.reshape(ctx.shape), gp, None, None
 
 
 def _schedule_dict(s):

@@ -111,22 +111,6 @@ namespace {
 // Result kinds the owner lane passes to the write-back of its slice.
 enum { KIND_MOMENT = 0, KIND_IC_G = 1, KIND_IC_KEEP = 2, KIND_NONE = 3 };
 
-// Fills f with the LDL^T of the slice Schur complement at the solution (no inertia shift).
-__device__ __forceinline__ void slice_factor_at(const SliceIn<double> &d, const SliceZ<double> &z,
-                                                const SliceEval<double> &e, SliceFactor &out) {
-  double s00, s01, s02, s11, s12, s22;
-  slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
-  Ldl3<double> f;
-  if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-    f.d0 = f.d1 = f.d2 = 0.0;
-    f.l10 = f.l20 = f.l21 = 0.0;
-  }
-  out.w = e.alpha;
-  out.wb = e.beta;
-  out.d0 = f.d0; out.d1 = f.d1; out.d2 = f.d2;
-  out.l10 = f.l10; out.l20 = f.l20; out.l21 = f.l21;
-}
-
 // ---------------------------------------------------------------------------------------
 // Moment path.  Requires u0 = u_hat, nx even, u_hat / u 16-byte aligned.
 // ---------------------------------------------------------------------------------------
@@ -134,7 +118,7 @@ __global__ void __launch_bounds__(128)
 k1d_moment(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
            const SampleDerived *__restrict__ sd, double *__restrict__ u,
            double *__restrict__ lam, BlockStat *__restrict__ bst,
-           SliceFactor *__restrict__ cache, SolverOpts o) {
+           SolverOpts o) {
   const int lane = threadIdx.x & 31;
   const int q = lane >> 3;        // group: slice 4*rho + q of a round
   const int r = lane & 7;         // lane within the group
@@ -257,7 +241,6 @@ k1d_moment(Geom1D g, int B, const double *__restrict__ uh, const double *__restr
         if (g.off_mass >= 0) lb[g.off_mass + k] = z.lm;
         if (g.off_energy >= 0) lb[g.off_energy + k] = z.le;
         if (g.off_bound >= 0) lb[g.off_bound + k] = z.lb;
-        if (cache) slice_factor_at(d, z, e, cache[s]);
       }
       bst[s] = st;
     }
@@ -410,7 +393,7 @@ __global__ void __launch_bounds__(128)
 k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
             const double *__restrict__ u0, const SampleDerived *__restrict__ sd,
             double *__restrict__ u, double *__restrict__ lam, BlockStat *__restrict__ bst,
-            SliceFactor *__restrict__ cache, SolverOpts o) {
+            SolverOpts o) {
   const int lane = threadIdx.x & 31;
   const long long total = (long long)B * g.nt;
   const int wpb = blockDim.x >> 5;
@@ -608,22 +591,6 @@ k1d_general(Geom1D g, int B, const double *__restrict__ uh, const double *__rest
       }
     }
     obj = warp_sum(obj);
-    if (cache) {
-      double s00, s01, s02, s11, s12, s22, v0, v1, v2;
-      gen_schur<NPL>(g, d, U, G, e, e.alpha, e.beta, s00, s01, s02, s11, s12, s22, v0, v1, v2, lane);
-      Ldl3<double> f;
-      if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-        f.d0 = f.d1 = f.d2 = 0.0;
-        f.l10 = f.l20 = f.l21 = 0.0;
-      }
-      if (lane == 0) {
-        SliceFactor sf;
-        sf.w = e.alpha; sf.wb = e.beta;
-        sf.d0 = f.d0; sf.d1 = f.d1; sf.d2 = f.d2;
-        sf.l10 = f.l10; sf.l20 = f.l20; sf.l21 = f.l21;
-        cache[s] = sf;
-      }
-    }
     if (lane == 0) {
       st.iters = iters;
       st.backtracks = nbt;
@@ -734,12 +701,12 @@ __global__ void k1d_backward_params(Geom1D g, int B, const double *__restrict__ 
 template <int NPL>
 void launch_general(const Geom1D &g, int B, const double *uh, const double *params,
                     const double *u0, const SampleDerived *sd, double *u, double *lam,
-                    BlockStat *bst, SliceFactor *cache, const SolverOpts &o, cudaStream_t s) {
+                    BlockStat *bst, const SolverOpts &o, cudaStream_t s) {
   const long long total = (long long)B * g.nt;
   const int threads = 128;
   long long blocks = (total + 3) / 4;
   if (blocks > 148LL * 64) blocks = 148LL * 64;
-  k1d_general<NPL><<<(int)blocks, threads, 0, s>>>(g, B, uh, params, u0, sd, u, lam, bst, cache, o);
+  k1d_general<NPL><<<(int)blocks, threads, 0, s>>>(g, B, uh, params, u0, sd, u, lam, bst, o);
 }
 
 template <int NPL>
@@ -795,7 +762,7 @@ static int warps_blocks(int nwarps) { return (nwarps * 32 + 127) / 128; }
 
 cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
                               const double *params, const double *u0, double *u, double *lambda,
-                              snap_stats *stats, void *cache, const SolverOpts &o, int path,
+                              snap_stats *stats, const SolverOpts &o, int path,
                               void *ws, cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
@@ -807,7 +774,7 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   launches++;
   if (mixed) {
     const int pid = snap_prof_begin(s, "k1d_mixed");
-    launch_1d_mixed(g, B, u_hat, params, w.sd, u, lambda, w.bst, (SliceFactor *)cache, o, 0, s);
+    launch_1d_mixed(g, B, u_hat, params, w.sd, u, lambda, w.bst, o, 0, s);
     snap_prof_end(s, pid);
   } else if (path == SNAP_PATH_MOMENT) {
     const long long ntiles = ((long long)B * g.nt + 31) / 32;
@@ -815,12 +782,12 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
     if (blocks > 148LL * 64) blocks = 148LL * 64;
     const int pid = snap_prof_begin(s, "k1d_moment");
     k1d_moment<<<(int)blocks, 128, 0, s>>>(g, B, u_hat, params, w.sd, u, lambda, w.bst,
-                                           (SliceFactor *)cache, o);
+                                           o);
     snap_prof_end(s, pid);
   } else {
     const int pid = snap_prof_begin(s, "k1d_general");
     SNAP_DISPATCH_NPL(g.nx, launch_general, g, B, u_hat, params, u0, w.sd, u, lambda, w.bst,
-                      (SliceFactor *)cache, o, s);
+                      o, s);
     snap_prof_end(s, pid);
   }
   launches++;
@@ -851,7 +818,7 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
 
 cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_u,
                                const double *u, const double *lambda, const double *params,
-                               const snap_stats *stats, const void *cache, double *grad_u_hat,
+                               const snap_stats *stats, double *grad_u_hat,
                                double *grad_params, void *ws, cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
@@ -859,7 +826,7 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
                                              nullptr, 0.0, grad_u_hat, w.contrib, grad_params,
                                              stats);
   const int pid = snap_prof_begin(s, "k1d_bwd_mixed");
-  launch_1d_bwd_mixed(g, B, grad_u, u, lambda, params, stats, w.sd, (const SliceFactor *)cache,
+  launch_1d_bwd_mixed(g, B, grad_u, u, lambda, params, stats, w.sd,
                       grad_u_hat, grad_params, w.contrib, s);
   snap_prof_end(s, pid);
   int launches = 2;

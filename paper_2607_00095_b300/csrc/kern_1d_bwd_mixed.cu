@@ -18,7 +18,6 @@ struct DirectBwd {
   const double *gu, *u, *lam;
   const snap_stats *fst;
   const SampleDerived *sd;
-  const SliceFactor *cache;
   double *gh, *gp;
   BwdContrib *contrib;
   __device__ __forceinline__ int sample(long long s) const { return (int)(s / nt); }
@@ -34,9 +33,6 @@ struct DirectBwd {
     return fst && fst[sample(s)].status != SNAP_SAMPLE_OK;
   }
   __device__ __forceinline__ SampleDerived derived(long long s) const { return sd[sample(s)]; }
-  __device__ __forceinline__ const SliceFactor *factor(long long s) const {
-    return cache ? cache + s : nullptr;
-  }
   __device__ __forceinline__ BwdContrib *contrib_at(long long s) const { return contrib + s; }
   __device__ __forceinline__ double *gp_of(long long s) const {
     return gp ? gp + (size_t)sample(s) * n_params : nullptr;
@@ -51,25 +47,26 @@ struct DirectBwd {
 __global__ void __launch_bounds__(128, 4)
 k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__restrict__ u,
               const double *__restrict__ lam, const snap_stats *__restrict__ fst,
-              const SampleDerived *__restrict__ sd, const SliceFactor *__restrict__ cache,
-              double *__restrict__ gh, double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
+              const SampleDerived *__restrict__ sd, double *__restrict__ gh,
+              double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
   const long long total = (long long)B * g.nt;
   const long long ntiles = (total + 31) >> 5;
   const int wpb = blockDim.x >> 5;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  const DirectBwd ad{total, g.nt, g.nx, g.n_rows, g.n_params, gu, u, lam, fst, sd, cache,
-                     gh, gp, contrib};
+  const DirectBwd ad{total, g.nt, g.nx, g.n_rows, g.n_params, gu, u, lam, fst, sd, gh, gp,
+                     contrib};
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb)
-    bwd_tile(g, ad, tile << 5, cache == nullptr);
+    bwd_tile(g, ad, tile << 5);
 }
 
 }  // namespace
 
 void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const double *u,
                          const double *lambda, const double *params, const snap_stats *stats,
-                         const SampleDerived *sd, const SliceFactor *cache, double *grad_u_hat,
-                         double *grad_params, BwdContrib *contrib, cudaStream_t s) {
+                         const SampleDerived *sd, double *grad_u_hat, double *grad_params,
+                         BwdContrib *contrib, cudaStream_t s) {
+  (void)params;
   const long long ntiles = ((long long)B * g.nt + 31) / 32;
   long long blocks = (ntiles + 3) / 4;
   if (blocks > 148LL * 64) blocks = 148LL * 64;
@@ -83,7 +80,6 @@ void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const dou
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  (void)params;
-  cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, stats, sd, cache,
-                     grad_u_hat, grad_params, contrib);
+  cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, stats, sd, grad_u_hat,
+                     grad_params, contrib);
 }

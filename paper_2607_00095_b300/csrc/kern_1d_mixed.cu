@@ -54,8 +54,7 @@ __device__ __forceinline__ df64 shfl_df(df64 v, int off) {
 __global__ void __launch_bounds__(64, 8)
 k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
           const SampleDerived *__restrict__ sd, double *__restrict__ u,
-          double *__restrict__ lam, BlockStat *__restrict__ bst,
-          SliceFactor *__restrict__ cache, SolverOpts o) {
+          double *__restrict__ lam, BlockStat *__restrict__ bst, SolverOpts o) {
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2;        // group: slice 8*rho + q of round rho
   const int r = lane & 3;         // lane within the group
@@ -171,7 +170,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
       kind = KIND_MOMENT;
       t1_solve_slice(g, k, m1, m2, mmx, mmn, mok, __ldg(row), __ldg(row + ih), row,
                      params + (size_t)b * g.n_params, sd[b], lam + (size_t)b * g.n_rows, bst + s,
-                     cache ? cache + s : nullptr, o, so_f, so_d, dxd, A, Cc, P0, PH);
+                     o, so_f, so_d, dxd, A, Cc, P0, PH);
     }
     // ---------------- phase 3: write-back, 4 lanes per slice ----------------
 #pragma unroll 1
@@ -215,7 +214,7 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
 
 void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *params,
                      const SampleDerived *sd, double *u, double *lambda, BlockStat *bst,
-                     SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s) {
+                     const SolverOpts &o, int blocks_per_sm, cudaStream_t s) {
   const long long ntiles = ((long long)B * g.nt + 31) / 32;
   long long blocks = (ntiles + 1) / 2;
   if (blocks_per_sm > 0 && blocks > 148LL * blocks_per_sm) blocks = 148LL * blocks_per_sm;
@@ -230,5 +229,5 @@ void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k1d_mixed, g, B, u_hat, params, sd, u, lambda, bst, cache, o);
+  cudaLaunchKernelEx(&cfg, k1d_mixed, g, B, u_hat, params, sd, u, lambda, bst, o);
 }

@@ -308,15 +308,13 @@ size_t ws_bytes_2d(const snap_problem *p, int B) {
          snap_align256(sizeof(double) * nfr);
 }
 
-size_t cache_bytes_2d(const snap_problem *p, int B) { (void)p; (void)B; return 0; }
 
 static int warps_blocks2(int nwarps) { return (nwarps * 32 + 127) / 128; }
 
 cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
                               const double *params, const double *w0, double *w, double *lambda,
-                              snap_stats *stats, void *cache, const SolverOpts &o, int path,
+                              snap_stats *stats, const SolverOpts &o, int path,
                               void *ws, cudaStream_t s) {
-  (void)cache;
   (void)path;
   if (w0) return cudaErrorNotSupported;
   cudaError_t eu = ensure_2d(p);
@@ -346,9 +344,8 @@ cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
 
 cudaError_t launch_2d_backward(const snap_problem *p, int B, const double *grad_w,
                                const double *w, const double *lambda, const double *params,
-                               const snap_stats *stats, const void *cache, double *grad_w_hat,
+                               const snap_stats *stats, double *grad_w_hat,
                                double *grad_params, void *ws, cudaStream_t s) {
-  (void)cache;
   cudaError_t eu = ensure_2d(p);
   if (eu != cudaSuccess) return eu;
   Ws2D wk = carve_2d(p, B, ws);

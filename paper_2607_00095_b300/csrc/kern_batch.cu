@@ -119,7 +119,6 @@ struct BatchTiles {
     return sdw[inst_of(s) - c->first_inst];
   }
   __device__ __forceinline__ BlockStat *stat(long long s) const { return c->bst + (int)s; }
-  __device__ __forceinline__ SliceFactor *factor(long long) const { return nullptr; }
   __device__ __forceinline__ void prefetch(long long s0l, long long s1l, int lane) const {
     const int s0 = (int)s0l, s1 = (int)s1l, n = nt();
     for (int i = s0 / n; i * n < s1; ++i) {
@@ -338,7 +337,6 @@ struct BatchBwdTiles {
   __device__ __forceinline__ SampleDerived derived(long long s) const {
     return sdw[inst_of(s) - c->first_inst];
   }
-  __device__ __forceinline__ const SliceFactor *factor(long long) const { return nullptr; }
   __device__ __forceinline__ BwdContrib *contrib_at(long long s) const { return contrib + (int)s; }
   __device__ __forceinline__ double *gp_of(long long s) const { return bwd[id_of(s)].gp; }
   // the tile's instances: derived values into the warp's table; the IC block of an instance
@@ -470,7 +468,7 @@ __device__ __forceinline__ void batch_1d_bwd(const BwdArgs &a, SampleDerived *sd
     ad.c = cx;
     ad.s0 = w.s0;
     ad.s1 = w.s1;
-    bwd_tile(cx->g, ad, w.s0, true);
+    bwd_tile(cx->g, ad, w.s0);
     // arrival: every lane's contributions and outputs are fenced before lane 0 counts
     __threadfence();
     __syncwarp();
@@ -928,10 +926,10 @@ SNAP_API snap_status snap_batch_project_grouped(snap_batch_t b, const snap_optio
     const int n = (int)b->group_inst[k].size();
     cudaError_t e;
     if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
-      e = launch_2d_forward(p, n, r.uh, r.params, nullptr, r.u, r.lam, r.stats, nullptr, so,
+      e = launch_2d_forward(p, n, r.uh, r.params, nullptr, r.u, r.lam, r.stats, so,
                             SNAP_PATH_MIXED, workspace, (cudaStream_t)stream);
     else
-      e = launch_1d_forward(p, n, r.uh, r.params, nullptr, r.u, r.lam, r.stats, nullptr, so,
+      e = launch_1d_forward(p, n, r.uh, r.params, nullptr, r.u, r.lam, r.stats, so,
                             SNAP_PATH_MIXED, workspace, (cudaStream_t)stream);
     if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   }
@@ -1115,11 +1113,11 @@ SNAP_API snap_status snap_batch_project_backward_grouped(snap_batch_t b, void *w
     const int n = (int)b->group_inst[k].size();
     cudaError_t e;
     if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
-      e = launch_2d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, nullptr, w.gh, w.gp,
-                             workspace, (cudaStream_t)stream);
+      e = launch_2d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, w.gh, w.gp, workspace,
+                             (cudaStream_t)stream);
     else
-      e = launch_1d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, nullptr, w.gh, w.gp,
-                             workspace, (cudaStream_t)stream);
+      e = launch_1d_backward(p, n, w.gu, r.u, r.lam, r.params, r.stats, w.gh, w.gp, workspace,
+                             (cudaStream_t)stream);
     if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   }
   return SNAP_OK;

@@ -133,14 +133,14 @@ SNAP_API snap_status snap_pcfm_sample(snap_problem_t p, int B, int n_steps, doub
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {
       if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
-        e = launch_2d_forward(p, B, uh, params, nullptr, u, lambda, stats, nullptr, so,
+        e = launch_2d_forward(p, B, uh, params, nullptr, u, lambda, stats, so,
                               SNAP_PATH_MIXED, pws, s);
       else if (p->desc.family == SNAP_FAMILY_D_BURGERS_BC)
         e = launch_1dbc_forward(p, B, uh, params, u, lambda, stats, so, pws, s);
       else if (p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX)
         e = launch_1dflux_forward(p, B, uh, params, u, lambda, stats, so, pws, s);
       else
-        e = launch_1d_forward(p, B, uh, params, nullptr, u, lambda, stats, nullptr, so,
+        e = launch_1d_forward(p, B, uh, params, nullptr, u, lambda, stats, so,
                               SNAP_PATH_MIXED, pws, s);
     }
     if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));

@@ -491,22 +491,9 @@ snap_status snap_workspace_size(snap_problem_t p, int B, size_t *bytes) {
   return SNAP_OK;
 }
 
-snap_status snap_adjoint_cache_size(snap_problem_t p, int B, size_t *bytes) {
-  if (!bytes) return fail(SNAP_ERR_INVALID_ARG, "null output");
-  snap_status st = check_batch(p, B);
-  if (st != SNAP_OK) return st;
-  if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) *bytes = cache_bytes_2d(p, B);
-  else if (p->desc.family == SNAP_FAMILY_TOY_LEFT_RIEMANN ||
-           p->desc.family == SNAP_FAMILY_D_BURGERS_BC ||
-           p->desc.family == SNAP_FAMILY_E_BURGERS_FLUX ||
-           p->desc.family == SNAP_FAMILY_F_HEAT_ENERGY) *bytes = 0;
-  else *bytes = sizeof(SliceFactor) * (size_t)B * p->g1.nt;
-  return SNAP_OK;
-}
-
 snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const double *params,
                          const double *u0, double *u, double *lambda, snap_stats *stats,
-                         void *adjoint_cache, const snap_options *opt, void *workspace,
+                         const snap_options *opt, void *workspace,
                          size_t workspace_bytes, snap_stream_t stream) {
   g_err[0] = 0;
   g_launches = 0;
@@ -547,11 +534,11 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
     e = launch_1dflux_forward(p, B, u_hat, params, u, lambda, stats, so, workspace,
                               (cudaStream_t)stream);
   } else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
-    e = launch_2d_forward(p, B, u_hat, params, u0, u, lambda, stats, adjoint_cache, so, path,
-                          workspace, (cudaStream_t)stream);
+    e = launch_2d_forward(p, B, u_hat, params, u0, u, lambda, stats, so, path, workspace,
+                          (cudaStream_t)stream);
   else
-    e = launch_1d_forward(p, B, u_hat, params, u0, u, lambda, stats, adjoint_cache, so, path,
-                          workspace, (cudaStream_t)stream);
+    e = launch_1d_forward(p, B, u_hat, params, u0, u, lambda, stats, so, path, workspace,
+                          (cudaStream_t)stream);
   if (e == cudaErrorNotSupported) return fail(SNAP_ERR_UNSUPPORTED, "unsupported request for this family");
   if (e != cudaSuccess) return cuda_fail(e, "snap_project launch");
   return SNAP_OK;
@@ -559,8 +546,8 @@ snap_status snap_project(snap_problem_t p, int B, const double *u_hat, const dou
 
 snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
                                   const double *u, const double *lambda, const double *params,
-                                  const snap_stats *stats, const void *adjoint_cache,
-                                  double *grad_u_hat, double *grad_params, void *workspace,
+                                  const snap_stats *stats, double *grad_u_hat,
+                                  double *grad_params, void *workspace,
                                   size_t workspace_bytes, snap_stream_t stream) {
   g_err[0] = 0;
   g_launches = 0;
@@ -587,11 +574,11 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
     e = launch_1dflux_backward(p, B, grad_u, u, stats, grad_u_hat, grad_params, workspace,
                                (cudaStream_t)stream);
   else if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY)
-    e = launch_2d_backward(p, B, grad_u, u, lambda, params, stats, adjoint_cache, grad_u_hat,
-                           grad_params, workspace, (cudaStream_t)stream);
+    e = launch_2d_backward(p, B, grad_u, u, lambda, params, stats, grad_u_hat, grad_params,
+                           workspace, (cudaStream_t)stream);
   else
-    e = launch_1d_backward(p, B, grad_u, u, lambda, params, stats, adjoint_cache, grad_u_hat,
-                           grad_params, workspace, (cudaStream_t)stream);
+    e = launch_1d_backward(p, B, grad_u, u, lambda, params, stats, grad_u_hat, grad_params,
+                           workspace, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "snap_project_backward launch");
   return SNAP_OK;
 }

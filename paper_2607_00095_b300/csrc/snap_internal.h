@@ -69,12 +69,6 @@ struct BwdContrib {
   double bm, bex, bfl, br;
 };
 
-// Adjoint cache per 1-D slice: W diagonal (interior, boundary) and the LDL^T of the 3x3
-// Schur complement S = J W^-1 J^T at the solution.
-struct SliceFactor {
-  double w, wb, d0, d1, d2, l10, l20, l21;
-};
-
 struct snap_problem {
   snap_problem_desc desc;
   snap_info info;
@@ -105,35 +99,35 @@ void snap_prof_end(cudaStream_t s, int id);
 // Host-side launchers (kern_1d.cu / kern_2d.cu).
 cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
                               const double *params, const double *u0, double *u, double *lambda,
-                              snap_stats *stats, void *cache, const SolverOpts &o, int path,
-                              void *ws, cudaStream_t s);
+                              snap_stats *stats, const SolverOpts &o, int path, void *ws,
+                              cudaStream_t s);
 cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_u,
                                const double *u, const double *lambda, const double *params,
-                               const snap_stats *stats, const void *cache, double *grad_u_hat,
-                               double *grad_params, void *ws, cudaStream_t s);
+                               const snap_stats *stats, double *grad_u_hat, double *grad_params,
+                               void *ws, cudaStream_t s);
 cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
                                const double *params, double *h, double *h_inf, void *ws,
                                cudaStream_t s);
 size_t ws_bytes_1d(const snap_problem *p, int B);
 void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const double *u,
                          const double *lambda, const double *params, const snap_stats *stats,
-                         const SampleDerived *sd, const SliceFactor *cache, double *grad_u_hat,
-                         double *grad_params, BwdContrib *contrib, cudaStream_t s);
+                         const SampleDerived *sd, double *grad_u_hat, double *grad_params,
+                         BwdContrib *contrib, cudaStream_t s);
 void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *params,
                      const SampleDerived *sd, double *u, double *lambda, BlockStat *bst,
-                     SliceFactor *cache, const SolverOpts &o, int blocks_per_sm, cudaStream_t s);
+                     const SolverOpts &o, int blocks_per_sm, cudaStream_t s);
 
 cudaError_t setup_2d(snap_problem *p);
 cudaError_t ensure_2d_factor(const snap_problem *p);
 void teardown_2d(snap_problem *p);
 cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
                               const double *params, const double *w0, double *w, double *lambda,
-                              snap_stats *stats, void *cache, const SolverOpts &o, int path,
-                              void *ws, cudaStream_t s);
+                              snap_stats *stats, const SolverOpts &o, int path, void *ws,
+                              cudaStream_t s);
 cudaError_t launch_2d_backward(const snap_problem *p, int B, const double *grad_w,
                                const double *w, const double *lambda, const double *params,
-                               const snap_stats *stats, const void *cache, double *grad_w_hat,
-                               double *grad_params, void *ws, cudaStream_t s);
+                               const snap_stats *stats, double *grad_w_hat, double *grad_params,
+                               void *ws, cudaStream_t s);
 cudaError_t launch_2d_residual(const snap_problem *p, int B, const double *w,
                                const double *params, double *h, double *h_inf, void *ws,
                                cudaStream_t s);
@@ -141,7 +135,6 @@ size_t ws_bytes_2d(const snap_problem *p, int B);
 bool supported_2d(int N);
 void launch_finalize_stats(int B, int nblk, const BlockStat *bst, double tol_h, snap_stats *stats,
                            cudaStream_t s);
-size_t cache_bytes_2d(const snap_problem *p, int B);
 
 // Family D (kern_1dbc.cu).
 size_t ws_bytes_1dbc(const snap_problem *p, int B);

@@ -88,7 +88,7 @@ SNAP_API snap_status snap_project_noalloc(snap_problem_t p, int B, const double 
   so.max_backtracks = o.max_backtracks;
   so.max_corrections = o.max_corrections;
   so.pad = 0;
-  const cudaError_t e = launch_1d_forward(p, B, u_hat, params, nullptr, u, lambda, stats, nullptr,
+  const cudaError_t e = launch_1d_forward(p, B, u_hat, params, nullptr, u, lambda, stats,
                                           so, o.path, scratch, (cudaStream_t)stream);
   if (e == cudaErrorNotSupported)
     return snap_fail_msg(SNAP_ERR_UNSUPPORTED, "unsupported request for this family");

@@ -27,7 +27,6 @@
 //   row_in(s) / row_out(s)  u_hat / u of slice s;  slice_k(s)  its time index;
 //   par(s) / lam_of(s)      the parameters / multipliers of its sample;
 //   derived(s)              the sample's SampleDerived;  stat(s)  its BlockStat slot;
-//   factor(s)               its adjoint-cache slot or nullptr;
 //   prefetch(s0, s1, lane)  L2 prefetch of the tile's u_hat;
 //   before_solve(s0, s1, lane)  hook run by the whole warp between phases 1 and 2.
 #pragma once
@@ -63,14 +62,13 @@ __device__ __forceinline__ df64 t1_shfl_df(df64 v, int off) {
 // Phase 2 for one slice k >= 1 (one lane): the slice's Newton-KKT iteration from its interior
 // moments (m1, m2: S1, S2 in double-float; mmx, mmn: interior extremes; mok: every value in
 // the float-pair range), u_hat at i = 0 and i = nx/2 (uh0, uhh) and the sample's derived
-// values; writes the slice's multipliers into lb, its statistics into *stat and, when cf is
-// not null, its adjoint factor.  Returns u = A u_hat + Cc on the interior, P0 / PH at i = 0 /
+// values; writes the slice's multipliers into lb and its statistics into *stat.  Returns u = A u_hat + Cc on the interior, P0 / PH at i = 0 /
 // nx/2.  row (u_hat of the slice, any address space) is read only by the FP64 fallback.
 __device__ __forceinline__ void t1_solve_slice(
     const Geom1D &g, int k, const df64 &m1, const df64 &m2, float mmx, float mmn, int mok,
     double uh0, double uhh, const double *row, const double *__restrict__ pg,
     const SampleDerived &dv, double *__restrict__ lb, BlockStat *__restrict__ stat,
-    SliceFactor *__restrict__ cf, const SolverOpts &o, const SliceOptsT<float> &so_f,
+    const SolverOpts &o, const SliceOptsT<float> &so_f,
     const SliceOptsT<df64> &so_d, const df64 &dxd, double &A, double &Cc, double &P0,
     double &PH) {
   const int nx = g.nx, ih = g.ih;
@@ -128,23 +126,6 @@ __device__ __forceinline__ void t1_solve_slice(
     st.obj = (double)obj;
     if (e.res != e.res) st.kkt_inf = NAN;
     if (hmx != hmx) st.h_inf = NAN;
-    if (cf) {
-      const double al = (double)e.alpha, be = (double)e.beta;
-      S1d = (double)m1; S2d = (double)m2;
-      SliceIn<double> d64 = slice_in_cast<double>(d);
-      SliceZ<double> z64{A, Cc, P0, PH, lmd, led, lbd};
-      double s00, s01, s02, s11, s12, s22;
-      slice_schur(d64, z64, A * S1d + Cc * (double)(nx - 2),
-                  A * A * S2d + 2.0 * A * Cc * S1d + Cc * Cc * (double)(nx - 2), 1.0 / al,
-                  1.0 / be, s00, s01, s02, s11, s12, s22);
-      Ldl3<double> f;
-      if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-        f.d0 = f.d1 = f.d2 = 0.0;
-        f.l10 = f.l20 = f.l21 = 0.0;
-      }
-      SliceFactor sf{al, be, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-      *cf = sf;
-    }
   } else {
     // FP64 fallback: moments in FP64 by this lane, FP64 iteration
     double a1 = 0.0, a2 = 0.0, mx = -INFINITY, mn = INFINITY;
@@ -187,17 +168,6 @@ __device__ __forceinline__ void t1_solve_slice(
     lmd = z.lm; led = z.le; lbd = z.lb;
     hm = e.hm; he = e.he; hb = e.hb; res = e.res;
     S1d = a1; S2d = a2;
-    if (cf) {
-      double s00, s01, s02, s11, s12, s22;
-      slice_schur(d, z, e.su, e.su2, 1.0 / e.alpha, 1.0 / e.beta, s00, s01, s02, s11, s12, s22);
-      Ldl3<double> f;
-      if (!ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-        f.d0 = f.d1 = f.d2 = 0.0;
-        f.l10 = f.l20 = f.l21 = 0.0;
-      }
-      SliceFactor sf{e.alpha, e.beta, f.d0, f.d1, f.d2, f.l10, f.l20, f.l21};
-      *cf = sf;
-    }
   }
   if (!range_ok) {
     st.iters = R.iters;
@@ -315,7 +285,7 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
       const double *row = ad.row_in(s);
       kind = T1_KIND_MOMENT;
       t1_solve_slice(g, k, m1, m2, mmx, mmn, mok, __ldg(row), __ldg(row + g.ih), row,
-                     ad.par(s), ad.derived(s), ad.lam_of(s), ad.stat(s), ad.factor(s), o, so_f,
+                     ad.par(s), ad.derived(s), ad.lam_of(s), ad.stat(s), o, so_f,
                      so_d, dxd, A, Cc, P0, PH);
     }
   }

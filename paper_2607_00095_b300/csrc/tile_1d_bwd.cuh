@@ -6,12 +6,13 @@
 // For every slice k >= 1 the adjoint solves K [a; b] = [gbar; 0] with the KKT matrix of
 // Appendix B at the solution (W = diag(w interior, wb at i in {0, h})):
 //     S b = J W^-1 gbar,   a = W^-1 (gbar - J^T b),   S = J W^-1 J^T.
-// J W^-1 gbar needs the interior sums sum gbar_i and sum u_i gbar_i (and, when the forward
-// factor is not cached, sum u_i and sum u_i^2 to rebuild S):
+// J W^-1 gbar needs the interior sums sum gbar_i and sum u_i gbar_i, and S is rebuilt from
+// sum u_i and sum u_i^2 (storing the forward's factors and reading them back measured slower
+// than rebuilding S here):
 //   phase 1  (4 lanes per slice): float-pair split of u and gbar with integer operations only
 //            (|x - hi - lo| < 2^-46 |x|), double-float sums;
-//   phase 2  (one slice per lane): S b = v in double-float, from the cached FP64 LDL^T factor
-//            or from S rebuilt in double-float; the per-slice contributions to dL/dtheta;
+//   phase 2  (one slice per lane): S rebuilt and S b = v solved in double-float; the
+//            per-slice contributions to dL/dtheta;
 //   phase 3  (4 lanes per slice): a_i = gbar_i / w - (dx b_m + 2 dx u_i b_e) / w with two
 //            FP64 FMAs per element.
 // IC slices (a = 0) are not live: the caller writes them.  A slice whose values leave the
@@ -23,7 +24,6 @@
 //   row_u(s) / row_g(s)      u and dL/du of the slice;  row_out(s)  dL/du_hat of the slice
 //   lam_of(s)                the sample's multipliers;  bad(s)  its forward status is not OK
 //   derived(s)               the sample's SampleDerived
-//   factor(s)                the slice's adjoint-cache slot or nullptr
 //   contrib_at(s)            the slice's BwdContrib slot
 //   gp_of(s)                 the sample's dL/dparams row or nullptr
 //   before_solve(lane)       hook run by the whole warp between phases 1 and 2
@@ -77,9 +77,140 @@ __device__ __forceinline__ df64 tb_split_df(double x, bool &ok) {
   return df64(h, l);
 }
 
+// Coefficients of the write-back a_i = gbar_i iw + u_i kx + k0 (interior) and
+// gbar_i iwb + u_i kxb + k0b (i = 0, nx/2) of one slice.
+struct BwdCoef {
+  double iw, iwb, kx, k0, kxb, k0b;
+};
+
+// Phase 2 of one live slice s (one lane): S b = J W^-1 gbar from the slice's interior sums
+// (mg = sum gbar_i, mug = sum u_i gbar_i, mu / muu = sum u_i / u_i^2; mok: every value in the
+// float-pair range), the slice's rows urow / grow (any address
+// space: the boundary values, and the FP64 fallback, read them); writes the slice's
+// contribution to dL/dparams and its boundary-parameter gradient, returns the write-back
+// coefficients (NaN for a failed sample).
 template <class Bwd>
-__device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long long sbase,
-                                         bool need_s) {
+__device__ __forceinline__ BwdCoef bwd_slice(const Geom1D &g, const Bwd &ad, long long s,
+                                             const df64 &mg, const df64 &mug, const df64 &mu,
+                                             const df64 &muu, int mok, const double *urow,
+                                             const double *grow, const df64 &dxd) {
+  const int nx = g.nx, ih = g.ih;
+  BwdCoef out;
+  double ciw = 0.0, ciwb = 0.0, ckx = 0.0, ck0 = 0.0, ckxb = 0.0, ck0b = 0.0;
+  {
+  const int k = ad.slice_k(s);
+  const bool bad = ad.bad(s);
+  const double *lb = ad.lam_of(s);
+  const double u0 = urow[0], uhv = urow[ih], g0 = grow[0], ghv = grow[ih];
+  const double lme = (g.rows & SL_ENERGY) ? lb[g.off_energy + k] : 0.0;
+  const double lbb = (g.rows & SL_BOUND) ? lb[g.off_bound + k] : 0.0;
+  bool ok = mok;
+  const df64 U0 = tb_split_df(u0, ok), UH = tb_split_df(uhv, ok), G0 = tb_split_df(g0, ok), GH = tb_split_df(ghv, ok);
+  const df64 LE = tb_split_df(lme, ok), LB = tb_split_df(lbb, ok);
+  const df64 two(2.0f, 0.0f), one(1.0f, 0.0f), zero(0.0f, 0.0f);
+  double bm = 0.0, be = 0.0, bbv = 0.0, w = 1.0, wb = 1.0;
+  if (ok) {
+    const df64 W = one + two * dxd * LE;
+    const df64 WB = W + two * LB;
+    const df64 iw = df64(1.0f, 0.0f) / W, iwb = df64(1.0f, 0.0f) / WB;
+    // v = J W^-1 gbar
+    const df64 pg2 = U0 * G0 + UH * GH;
+    const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
+    const df64 v0 = hm ? dxd * (mg * iw + (G0 + GH) * iwb) : zero;
+    const df64 v1 = he ? two * dxd * (mug * iw + pg2 * iwb) : zero;
+    const df64 v2 = hbnd ? two * pg2 * iwb : zero;
+    Ldl3<df64> f;
+    SliceIn<df64> d;
+    d.dx = dxd;
+    d.n = df64((float)(nx - 2), 0.0f);
+    d.rows = g.rows;
+    d.nint = nx - 2;
+    SliceZ<df64> z;
+    z.p0 = U0; z.ph = UH;
+    df64 s00, s01, s02, s11, s12, s22;
+    slice_schur(d, z, mu, muu, iw, iwb, s00, s01, s02, s11, s12, s22);
+    if (ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
+      df64 xm, xe, xb;
+      ldl3_solve(f, v0, v1, v2, xm, xe, xb);
+      if (!hm) xm = zero;
+      if (!he) xe = zero;
+      if (!hbnd) xb = zero;
+      bm = (double)xm; be = (double)xe; bbv = (double)xb;
+      w = (double)W; wb = (double)WB;
+      // a = W^-1 (gbar - dx b_m - 2 dx u b_e [- 2 u b_b at the boundary])
+      const df64 kx = -(two * dxd * xe) * iw, k0 = -(dxd * xm) * iw;
+      const df64 kxb = -(two * dxd * xe + two * xb) * iwb, k0b = -(dxd * xm) * iwb;
+      ciw = (double)iw; ciwb = (double)iwb;
+      ckx = (double)kx; ck0 = (double)k0; ckxb = (double)kxb; ck0b = (double)k0b;
+    } else {
+      ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN;
+      bm = be = bbv = NAN;
+    }
+  } else {
+    // FP64 by this lane: sums, S and the solve
+    double sgd = 0.0, sugd = 0.0, sud = 0.0, suud = 0.0;
+    for (int i = 0; i < nx; ++i) {
+      if (i == 0 || i == ih) continue;
+      const double uv = urow[i], gv = grow[i];
+      sgd += gv;
+      sugd = fma(uv, gv, sugd);
+      sud += uv;
+      suud = fma(uv, uv, suud);
+    }
+    w = 1.0 + 2.0 * g.dx * lme;
+    wb = w + 2.0 * lbb;
+    const double iw = 1.0 / w, iwb = 1.0 / wb;
+    const double pg2 = u0 * g0 + uhv * ghv;
+    const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
+    const double v0 = hm ? g.dx * (sgd * iw + (g0 + ghv) * iwb) : 0.0;
+    const double v1 = he ? 2.0 * g.dx * (sugd * iw + pg2 * iwb) : 0.0;
+    const double v2 = hbnd ? 2.0 * pg2 * iwb : 0.0;
+    SliceIn<double> d;
+    d.dx = g.dx;
+    d.n = (double)(nx - 2);
+    d.rows = g.rows;
+    d.nint = nx - 2;
+    SliceZ<double> z;
+    z.p0 = u0; z.ph = uhv;
+    double s00, s01, s02, s11, s12, s22;
+    slice_schur(d, z, sud, suud, iw, iwb, s00, s01, s02, s11, s12, s22);
+    Ldl3<double> f;
+    if (ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
+      ldl3_solve(f, v0, v1, v2, bm, be, bbv);
+      if (!hm) bm = 0.0;
+      if (!he) be = 0.0;
+      if (!hbnd) bbv = 0.0;
+    } else {
+      bm = be = bbv = NAN;
+    }
+    ciw = iw; ciwb = iwb;
+    ckx = -2.0 * g.dx * be * iw; ck0 = -g.dx * bm * iw;
+    ckxb = -(2.0 * g.dx * be + 2.0 * bbv) * iwb; ck0b = -g.dx * bm * iwb;
+  }
+  if (bad) { ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN; }
+  out = BwdCoef{ciw, ciwb, ckx, ck0, ckxb, ck0b};
+  BwdContrib c{bm, 0.0, 0.0, 0.0};
+  if (g.rows & SL_ENERGY) {
+    const SampleDerived dv = ad.derived(s);
+    const double t = (double)k / (double)(g.nt - 1);
+    const double ex = (double)tb_df_pow(df64(dv.qh, dv.ql), k);
+    const bool expb = dv.E0 * ex >= dv.M * dv.M + g.energy_floor;
+    c.bex = expb ? be * ex : 0.0;
+    c.bfl = expb ? 0.0 : be;
+    c.br = expb ? -be * t * dv.E0 * ex : 0.0;
+  }
+  *ad.contrib_at(s) = c;
+  double *gpr = ad.gp_of(s);
+  if (gpr && (g.rows & SL_BOUND)) gpr[g.p_c + k] = bad ? NAN : bbv;
+  (void)w;
+  (void)wb;
+
+  }
+  return out;
+}
+
+template <class Bwd>
+__device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long long sbase) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2;
@@ -121,12 +252,10 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
           tb_acc2(sg, eg, gh1, gl1);
           tb_acc_prod(sug, eug, uh0, ul0, gh0, gl0);
           tb_acc_prod(sug, eug, uh1, ul1, gh1, gl1);
-          if (need_s) {
-            tb_acc2(su, eu, uh0, ul0);
-            tb_acc2(su, eu, uh1, ul1);
-            tb_acc_prod(suu, euu, uh0, ul0, uh0, ul0);
-            tb_acc_prod(suu, euu, uh1, ul1, uh1, ul1);
-          }
+          tb_acc2(su, eu, uh0, ul0);
+          tb_acc2(su, eu, uh1, ul1);
+          tb_acc_prod(suu, euu, uh0, ul0, uh0, ul0);
+          tb_acc_prod(suu, euu, uh1, ul1, uh1, ul1);
         }
       }
     }
@@ -136,10 +265,8 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
     for (int off = 1; off < 4; off <<= 1) {
       a_g = a_g + tb_shfl_df(a_g, off);
       a_ug = a_ug + tb_shfl_df(a_ug, off);
-      if (need_s) {
-        a_u = a_u + tb_shfl_df(a_u, off);
-        a_uu = a_uu + tb_shfl_df(a_uu, off);
-      }
+      a_u = a_u + tb_shfl_df(a_u, off);
+      a_uu = a_uu + tb_shfl_df(a_uu, off);
       ok &= __shfl_xor_sync(FULL, ok, off);
     }
     if (r == rho) { mg = a_g; mug = a_ug; mu = a_u; muu = a_uu; mok = ok; }
@@ -151,127 +278,8 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
   double ciw = 0.0, ciwb = 0.0, ckx = 0.0, ck0 = 0.0, ckxb = 0.0, ck0b = 0.0;
   if (ad.live(s)) {
     live = 1;
-    const int k = ad.slice_k(s);
-    const bool bad = ad.bad(s);
-    const double *lb = ad.lam_of(s);
-    const double *urow = ad.row_u(s);
-    const double *grow = ad.row_g(s);
-    const double u0 = urow[0], uhv = urow[ih], g0 = grow[0], ghv = grow[ih];
-    const double lme = (g.rows & SL_ENERGY) ? lb[g.off_energy + k] : 0.0;
-    const double lbb = (g.rows & SL_BOUND) ? lb[g.off_bound + k] : 0.0;
-    bool ok = mok;
-    const df64 U0 = tb_split_df(u0, ok), UH = tb_split_df(uhv, ok), G0 = tb_split_df(g0, ok), GH = tb_split_df(ghv, ok);
-    const df64 LE = tb_split_df(lme, ok), LB = tb_split_df(lbb, ok);
-    const df64 two(2.0f, 0.0f), one(1.0f, 0.0f), zero(0.0f, 0.0f);
-    double bm = 0.0, be = 0.0, bbv = 0.0, w = 1.0, wb = 1.0;
-    if (ok) {
-      const df64 W = one + two * dxd * LE;
-      const df64 WB = W + two * LB;
-      const df64 iw = df64(1.0f, 0.0f) / W, iwb = df64(1.0f, 0.0f) / WB;
-      // v = J W^-1 gbar
-      const df64 pg2 = U0 * G0 + UH * GH;
-      const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
-      const df64 v0 = hm ? dxd * (mg * iw + (G0 + GH) * iwb) : zero;
-      const df64 v1 = he ? two * dxd * (mug * iw + pg2 * iwb) : zero;
-      const df64 v2 = hbnd ? two * pg2 * iwb : zero;
-      Ldl3<df64> f;
-      bool fok;
-      const SliceFactor *cf = ad.factor(s);
-      if (cf) {
-        const SliceFactor c = *cf;
-        bool cok = true;
-        f.d0 = tb_split_df(c.d0, cok); f.d1 = tb_split_df(c.d1, cok); f.d2 = tb_split_df(c.d2, cok);
-        f.l10 = tb_split_df(c.l10, cok); f.l20 = tb_split_df(c.l20, cok); f.l21 = tb_split_df(c.l21, cok);
-        fok = cok && !(f.d0 == zero) && !(f.d1 == zero) && !(f.d2 == zero);
-        if (fok) {
-          f.i0 = one / f.d0; f.i1 = one / f.d1; f.i2 = one / f.d2;
-        }
-      } else {
-        SliceIn<df64> d;
-        d.dx = dxd;
-        d.n = df64((float)(nx - 2), 0.0f);
-        d.rows = g.rows;
-        d.nint = nx - 2;
-        SliceZ<df64> z;
-        z.p0 = U0; z.ph = UH;
-        df64 s00, s01, s02, s11, s12, s22;
-        slice_schur(d, z, mu, muu, iw, iwb, s00, s01, s02, s11, s12, s22);
-        fok = ldl3_factor(s00, s01, s02, s11, s12, s22, f);
-      }
-      if (fok) {
-        df64 xm, xe, xb;
-        ldl3_solve(f, v0, v1, v2, xm, xe, xb);
-        if (!hm) xm = zero;
-        if (!he) xe = zero;
-        if (!hbnd) xb = zero;
-        bm = (double)xm; be = (double)xe; bbv = (double)xb;
-        w = (double)W; wb = (double)WB;
-        // a = W^-1 (gbar - dx b_m - 2 dx u b_e [- 2 u b_b at the boundary])
-        const df64 kx = -(two * dxd * xe) * iw, k0 = -(dxd * xm) * iw;
-        const df64 kxb = -(two * dxd * xe + two * xb) * iwb, k0b = -(dxd * xm) * iwb;
-        ciw = (double)iw; ciwb = (double)iwb;
-        ckx = (double)kx; ck0 = (double)k0; ckxb = (double)kxb; ck0b = (double)k0b;
-      } else {
-        ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN;
-        bm = be = bbv = NAN;
-      }
-    } else {
-      // FP64 by this lane: sums, S and the solve
-      double sgd = 0.0, sugd = 0.0, sud = 0.0, suud = 0.0;
-      for (int i = 0; i < nx; ++i) {
-        if (i == 0 || i == ih) continue;
-        const double uv = urow[i], gv = grow[i];
-        sgd += gv;
-        sugd = fma(uv, gv, sugd);
-        sud += uv;
-        suud = fma(uv, uv, suud);
-      }
-      w = 1.0 + 2.0 * g.dx * lme;
-      wb = w + 2.0 * lbb;
-      const double iw = 1.0 / w, iwb = 1.0 / wb;
-      const double pg2 = u0 * g0 + uhv * ghv;
-      const bool hm = g.rows & SL_MASS, he = g.rows & SL_ENERGY, hbnd = g.rows & SL_BOUND;
-      const double v0 = hm ? g.dx * (sgd * iw + (g0 + ghv) * iwb) : 0.0;
-      const double v1 = he ? 2.0 * g.dx * (sugd * iw + pg2 * iwb) : 0.0;
-      const double v2 = hbnd ? 2.0 * pg2 * iwb : 0.0;
-      SliceIn<double> d;
-      d.dx = g.dx;
-      d.n = (double)(nx - 2);
-      d.rows = g.rows;
-      d.nint = nx - 2;
-      SliceZ<double> z;
-      z.p0 = u0; z.ph = uhv;
-      double s00, s01, s02, s11, s12, s22;
-      slice_schur(d, z, sud, suud, iw, iwb, s00, s01, s02, s11, s12, s22);
-      Ldl3<double> f;
-      if (ldl3_factor(s00, s01, s02, s11, s12, s22, f)) {
-        ldl3_solve(f, v0, v1, v2, bm, be, bbv);
-        if (!hm) bm = 0.0;
-        if (!he) be = 0.0;
-        if (!hbnd) bbv = 0.0;
-      } else {
-        bm = be = bbv = NAN;
-      }
-      ciw = iw; ciwb = iwb;
-      ckx = -2.0 * g.dx * be * iw; ck0 = -g.dx * bm * iw;
-      ckxb = -(2.0 * g.dx * be + 2.0 * bbv) * iwb; ck0b = -g.dx * bm * iwb;
-    }
-    if (bad) { ciw = ciwb = ckx = ck0 = ckxb = ck0b = NAN; }
-    BwdContrib c{bm, 0.0, 0.0, 0.0};
-    if (g.rows & SL_ENERGY) {
-      const SampleDerived dv = ad.derived(s);
-      const double t = (double)k / (double)(g.nt - 1);
-      const double ex = (double)tb_df_pow(df64(dv.qh, dv.ql), k);
-      const bool expb = dv.E0 * ex >= dv.M * dv.M + g.energy_floor;
-      c.bex = expb ? be * ex : 0.0;
-      c.bfl = expb ? 0.0 : be;
-      c.br = expb ? -be * t * dv.E0 * ex : 0.0;
-    }
-    *ad.contrib_at(s) = c;
-    double *gpr = ad.gp_of(s);
-    if (gpr && (g.rows & SL_BOUND)) gpr[g.p_c + k] = bad ? NAN : bbv;
-    (void)w;
-    (void)wb;
+    const BwdCoef cf = bwd_slice(g, ad, s, mg, mug, mu, muu, mok, ad.row_u(s), ad.row_g(s), dxd);
+    ciw = cf.iw; ciwb = cf.iwb; ckx = cf.kx; ck0 = cf.k0; ckxb = cf.kxb; ck0b = cf.k0b;
   }
   // ---------------- phase 3: a = W^-1 (gbar - J^T b), 4 lanes per slice ----------------
 #pragma unroll 1

@@ -32,14 +32,14 @@ def to_dev(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev())
 
 
-def run_gpu(prob, u_hat, params, u0=None, cache=False, **opt):
+def run_gpu(prob, u_hat, params, u0=None, **opt):
     B = u_hat.shape[0]
     uh = to_dev(u_hat.reshape(B, -1))
     pr = to_dev(params)
     u0d = to_dev(u0.reshape(B, -1)) if u0 is not None else None
-    u, lam, st, cb = prob.project(uh, pr, u0=u0d, opts=options(**opt), cache=cache)
+    u, lam, st = prob.project(uh, pr, u0=u0d, opts=options(**opt))
     torch.cuda.synchronize()
-    return (u.cpu().numpy(), lam.cpu().numpy(), decode_stats(st), cb,
+    return (u.cpu().numpy(), lam.cpu().numpy(), decode_stats(st),
             dict(uh=uh, pr=pr, u=u, lam=lam, st=st))
 
 

@@ -109,17 +109,17 @@ def test_null_and_size_errors_without_gpu():
     assert L.snap_workspace_size(p.handle, -1, C.byref(n)) == 1
     o = options()
     # B = 0 is a no-op even with null buffers
-    assert L.snap_project(p.handle, 0, None, None, None, None, None, None, None, C.byref(o), None, 0, None) == 0
+    assert L.snap_project(p.handle, 0, None, None, None, None, None, None, C.byref(o), None, 0, None) == 0
     # missing workspace is reported before any launch
     fake = C.c_void_p(1 << 20)
     rc = L.snap_project(p.handle, 2, fake, fake, None, C.c_void_p(2 << 20), C.c_void_p(3 << 20), None,
-                        None, C.byref(o), None, 0, None)
+                        C.byref(o), None, 0, None)
     assert rc == 5
     bad = options(tol_kkt=-1.0)
-    rc = L.snap_project(p.handle, 2, fake, fake, None, fake, fake, None, None, C.byref(bad), None, 0, None)
+    rc = L.snap_project(p.handle, 2, fake, fake, None, fake, fake, None, C.byref(bad), None, 0, None)
     assert rc == 1
     t = Problem("toy", 3, 3)
-    rc = L.snap_project(t.handle, 1, fake, fake, None, fake, fake, None, None, C.byref(o), None, 0, None)
+    rc = L.snap_project(t.handle, 1, fake, fake, None, fake, fake, None, C.byref(o), None, 0, None)
     assert rc == 2
 
 
@@ -130,10 +130,9 @@ def test_options_defaults_and_stats_layout():
     assert STATS_DTYPE.itemsize == C.sizeof(_abi.Stats) == 40
 
 
-def test_workspace_and_cache_sizes():
+def test_workspace_sizes():
     p = Problem("B", 128, 100)
     assert p.workspace_bytes(512) > p.workspace_bytes(1) > 0
-    assert p.cache_bytes(512) == 512 * 100 * 64
 
 
 @pytest.mark.parametrize("nx,nt,K", [(5, 4, 1), (12, 7, 3), (9, 3, 2)])

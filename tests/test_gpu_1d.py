@@ -26,7 +26,7 @@ def test_small_1d_workload_parity(path):
     nx, nt, B = w["nx"], w["nt"], w["B"]
     uh, pr = synthetic.gen_1d(w["seed"], B, nx, nt, "A")
     p = Problem("A", nx, nt)
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    u, lam, st, _ = H.run_gpu(p, uh, pr, path=path)
     ue, le, so, S, b = _oracle("A", nx, nt, pr, uh)
     assert (st["status"] == 0).all() and (so["status"] == 0).all()
     H.assert_u_close(u, ue)
@@ -45,7 +45,7 @@ def test_small_1d_workload_parity(path):
 def test_burgers_family_parity_ragged(path, B, nx, nt, seed):
     uh, pr = synthetic.gen_1d(seed, B, nx, nt, "B")
     p = Problem("B", nx, nt)
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    u, lam, st, _ = H.run_gpu(p, uh, pr, path=path)
     ue, le, so, S, b = _oracle("B", nx, nt, pr, uh)
     # every sample: the same outcome on both sides (a GPU that converges where the oracle
     # stalls, or the reverse, fails here), then the values of the converged ones
@@ -63,7 +63,7 @@ def test_burgers_full_size_sampled():
     nx, nt, B = w["nx"], w["nt"], w["B"]
     uh, pr = synthetic.gen_1d(w["seed"], B, nx, nt, "B")
     p = Problem("B", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     assert (st["status"] == 0).all()
     assert st["h_inf"].max() <= H.H_TOL
     # residual recomputed from the written u, on the GPU and on the host
@@ -84,9 +84,9 @@ def test_burgers_full_size_sampled():
 def test_paths_agree():
     uh, pr = synthetic.gen_1d(21, 16, 128, 33, "B")
     p = Problem("B", 128, 33)
-    um, lm, sm, _, _ = H.run_gpu(p, uh, pr, path="moment")
-    ug, lg, sg, _, _ = H.run_gpu(p, uh, pr, path="general")
-    ux, lx, sx, _, _ = H.run_gpu(p, uh, pr, path="mixed")
+    um, lm, sm, _ = H.run_gpu(p, uh, pr, path="moment")
+    ug, lg, sg, _ = H.run_gpu(p, uh, pr, path="general")
+    ux, lx, sx, _ = H.run_gpu(p, uh, pr, path="mixed")
     assert (sm["status"] == 0).all() and (sg["status"] == 0).all() and (sx["status"] == 0).all()
     S = problems.structure_1d("B", 128, 33)
     # the two FP64 paths run the same iteration: agreement to rounding
@@ -107,7 +107,7 @@ def test_mixed_path_falls_back_to_fp64_out_of_range():
         pr[s, :nx] *= scale
         pr[s, nx + 1:] *= scale * scale
     p = Problem("B", nx, nt)
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path="mixed")
+    u, lam, st, _ = H.run_gpu(p, uh, pr, path="mixed")
     ue, le, so, S, _ = _oracle("B", nx, nt, pr, uh)
     ok = so["status"] == 0
     assert ok[[0, 3]].all()
@@ -121,7 +121,7 @@ def test_general_path_with_start_point():
     rng = np.random.default_rng(32)
     u0 = uh + 0.05 * rng.normal(size=uh.shape)
     p = Problem("B", nx, nt)
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, u0=u0)          # auto -> general path
+    u, lam, st, _ = H.run_gpu(p, uh, pr, u0=u0)          # auto -> general path
     ue, le, so, S, _ = _oracle("B", nx, nt, pr, uh, u0=u0.reshape(B, -1))
     ok = so["status"] == 0
     np.testing.assert_array_equal(st["status"][ok], 0)
@@ -139,7 +139,7 @@ def test_row_subsets(rows, path):
     nx, nt, B = 32, 6, 3
     uh, pr = synthetic.gen_1d(41, B, nx, nt, "A")
     p = Problem("A", nx, nt, rows=rows)
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+    u, lam, st, _ = H.run_gpu(p, uh, pr, path=path)
     assert (st["status"] == 0).all()
     U = u.reshape(B, nt, nx)
     np.testing.assert_allclose(U[:, 0], pr[:, :nx], atol=1e-14)
@@ -165,13 +165,13 @@ def test_edge_cases_status_codes():
     pr[3, nx + 1] += 0.5                     # sample 3: c_0 inconsistent with the IC rows
     p = Problem("B", nx, nt)
     for path in PATHS:
-        u, lam, st, _, _ = H.run_gpu(p, uh, pr, path=path)
+        u, lam, st, _ = H.run_gpu(p, uh, pr, path=path)
         assert st["status"][0] == 0 and st["status"][4] == 0
         assert st["status"][1] == 3          # NONFINITE
         assert st["status"][2] == 4          # INFEASIBLE_PARAMS
         assert st["status"][3] == 5          # RESIDUAL
         assert np.isfinite(u[0]).all()
-    u, lam, st, _, _ = H.run_gpu(p, uh, pr, max_iter=1)
+    u, lam, st, _ = H.run_gpu(p, uh, pr, max_iter=1)
     assert st["status"][0] == 1              # MAXITER
 
 
@@ -179,7 +179,7 @@ def test_empty_batch_and_errors():
     p = Problem("B", 16, 4)
     x = torch.zeros(0, 64, dtype=torch.float64, device="cuda")
     prm = torch.zeros(0, p.n_params, dtype=torch.float64, device="cuda")
-    u, lam, st, _ = p.project(x, prm)
+    u, lam, st = p.project(x, prm)
     assert u.shape[0] == 0
     with pytest.raises(ValueError):
         p.project(torch.zeros(2, 64, dtype=torch.float64), torch.zeros(2, p.n_params, dtype=torch.float64))
@@ -189,11 +189,11 @@ def test_batch_permutation_bitwise_and_determinism():
     nx, nt, B = 64, 12, 7
     uh, pr = synthetic.gen_1d(61, B, nx, nt, "B")
     p = Problem("B", nx, nt)
-    u1, l1, s1, _, _ = H.run_gpu(p, uh, pr)
-    u2, l2, s2, _, _ = H.run_gpu(p, uh, pr)
+    u1, l1, s1, _ = H.run_gpu(p, uh, pr)
+    u2, l2, s2, _ = H.run_gpu(p, uh, pr)
     assert np.array_equal(u1, u2) and np.array_equal(l1, l2)
     perm = np.array([4, 0, 6, 2, 1, 5, 3])
-    u3, l3, s3, _, _ = H.run_gpu(p, uh[perm], pr[perm])
+    u3, l3, s3, _ = H.run_gpu(p, uh[perm], pr[perm])
     assert np.array_equal(u3, u1[perm]) and np.array_equal(l3, l1[perm])
 
 

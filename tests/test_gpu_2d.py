@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 def _gpu(N, nt, wh, pr, **kw):
     p = Problem("C", N, nt)
-    u, lam, st, cb, d = H.run_gpu(p, wh, pr, **kw)
+    u, lam, st, d = H.run_gpu(p, wh, pr, **kw)
     return p, u, lam, st, d
 
 

@@ -62,7 +62,7 @@ def _reference(probs, bufs):
     """snap_project on each group's contiguous block."""
     out = {}
     for pi, g in bufs.items():
-        u, lam, st, _ = probs[pi].project(g["uh"], g["pr"])
+        u, lam, st = probs[pi].project(g["uh"], g["pr"])
         torch.cuda.synchronize()
         out[pi] = (u.cpu().numpy(), lam.cpu().numpy(), st.cpu().numpy())
     return out

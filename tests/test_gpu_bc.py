@@ -24,7 +24,7 @@ def _oracle(nx, nt, pr, uh):
 def test_bc_against_oracle(nx, nt, B, seed):
     uh, pr = synthetic.gen_burgers_bc(seed, B, nx, nt)
     p = Problem("D", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= 1e-12
     assert (st["iters"] == 1).all()
     ue, le, so, S = _oracle(nx, nt, pr, uh)
@@ -44,7 +44,7 @@ def test_bc_full_size_sampled():
     B, nx, nt = w["B"], w["nx"], w["nt"]
     uh, pr = synthetic.gen_burgers_bc(w["seed"], B, nx, nt)
     p = Problem("D", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= 1e-12
     pick = [0, 77, 511]
     ue, le, so, S = _oracle(nx, nt, pr[pick], uh[pick])
@@ -60,7 +60,7 @@ def test_bc_edge_cases():
     uh[1] = ue.reshape(nt, nx)
     uh[2, 1, 5] = np.nan
     p = Problem("D", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr, tol_kkt=1e-12)
+    u, lam, st, d = H.run_gpu(p, uh, pr, tol_kkt=1e-12)
     assert st["status"][0] == 0 and st["iters"][0] == 1
     assert st["status"][1] == 0 and st["iters"][1] == 0
     np.testing.assert_array_equal(u[1], uh[1].ravel())
@@ -74,7 +74,7 @@ def test_bc_adjoint_against_oracle_and_fd():
     uh, pr = synthetic.gen_burgers_bc(87, B, nx, nt)
     gbar = synthetic.gen_gbar(88, (B, nx * nt))
     p = Problem("D", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     gh, gp = p.backward(H.to_dev(gbar), d["u"], d["lam"], d["pr"], stats=d["st"])
     torch.cuda.synchronize()
     gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
@@ -90,7 +90,7 @@ def test_bc_adjoint_against_oracle_and_fd():
     h = 1e-6
 
     def loss(prm, x):
-        uu, _, _, _, _ = H.run_gpu(p, x, prm)
+        uu, _, _, _ = H.run_gpu(p, x, prm)
         return (uu * gbar).sum(axis=1)
 
     for j in range(2):

@@ -22,7 +22,7 @@ def _check(nx, nt, K, B, seed, g_shift=0.0):
     uh, g = synthetic.gen_burgers_flux(seed, B, nx, nt)
     g = g + g_shift
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, d = H.run_gpu(p, uh, g)
+    u, lam, st, d = H.run_gpu(p, uh, g)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= 1e-12
     assert (st["iters"] == 1).all()
     ue, le, so = flux.project(nx, nt, K, g, uh.reshape(B, -1))
@@ -61,7 +61,7 @@ def test_flux_signed_data():
     uh, _ = synthetic.gen_burgers_flux(97, B, nx, nt)
     g = np.random.default_rng(98).uniform(-1, 1, size=(B, nx))
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, d = H.run_gpu(p, uh, g)
+    u, lam, st, d = H.run_gpu(p, uh, g)
     assert (st["status"] == 0).all()
     ue, le, _ = flux.project(nx, nt, K, g, uh.reshape(B, -1))
     np.testing.assert_array_equal(u[:, :(K + 1) * nx], ue[:, :(K + 1) * nx])
@@ -76,7 +76,7 @@ def test_flux_full_size_sampled(K):
     B, nx, nt = w["B"], w["nx"], w["nt"]
     uh, g = synthetic.gen_burgers_flux(w["seed"], B, nx, nt)
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, d = H.run_gpu(p, uh, g)
+    u, lam, st, d = H.run_gpu(p, uh, g)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= 1e-12
     pick = [0, 255, 511]
     ue, le, _ = flux.project(nx, nt, K, g[pick], uh[pick].reshape(len(pick), -1))
@@ -88,15 +88,15 @@ def test_flux_batch_independence_and_nan():
     nx, nt, K, B = 10, 24, 3, 6
     uh, g = synthetic.gen_burgers_flux(99, B, nx, nt)
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, _ = H.run_gpu(p, uh, g)
+    u, lam, st, _ = H.run_gpu(p, uh, g)
     perm = np.array([3, 0, 5, 1, 4, 2])
-    up, lp, sp, _, _ = H.run_gpu(p, uh[perm], g[perm])
+    up, lp, sp, _ = H.run_gpu(p, uh[perm], g[perm])
     np.testing.assert_array_equal(up, u[perm])
     np.testing.assert_array_equal(lp, lam[perm])
     uh2 = uh.copy()
     uh2[2, 1, 4] = np.nan          # a chain slice
     uh2[4, 18, 0] = np.nan         # a mass slice
-    u2, _, st2, _, _ = H.run_gpu(p, uh2, g)
+    u2, _, st2, _ = H.run_gpu(p, uh2, g)
     assert st2["status"][2] == 3 and st2["status"][4] == 3
     ok = [0, 1, 3, 5]
     assert (st2["status"][ok] == 0).all()
@@ -109,7 +109,7 @@ def test_flux_adjoint_against_oracle_and_fd():
     g = g + 0.05                   # flux arguments away from the switches of F
     gbar = synthetic.gen_gbar(101, (B, nx * nt))
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, d = H.run_gpu(p, uh, g)
+    u, lam, st, d = H.run_gpu(p, uh, g)
     gh, gp = p.backward(H.to_dev(gbar), d["u"], d["lam"], d["pr"], stats=d["st"])
     torch.cuda.synchronize()
     gh, gp = gh.cpu().numpy(), gp.cpu().numpy()
@@ -121,7 +121,7 @@ def test_flux_adjoint_against_oracle_and_fd():
     e = 1e-6
 
     def loss(gg, x):
-        uu, _, _, _, _ = H.run_gpu(p, x, gg)
+        uu, _, _, _ = H.run_gpu(p, x, gg)
         return (uu * gbar).sum(axis=1)
 
     for i in range(0, nx, 3):
@@ -142,7 +142,7 @@ def test_flux_adjoint_nan_for_failed_samples():
     uh[1, 4, 3] = np.nan
     gbar = synthetic.gen_gbar(103, (B, nx * nt))
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, d = H.run_gpu(p, uh, g)
+    u, lam, st, d = H.run_gpu(p, uh, g)
     assert st["status"][1] == 3
     gh, gp = p.backward(H.to_dev(gbar), d["u"], d["lam"], d["pr"], stats=d["st"])
     torch.cuda.synchronize()
@@ -165,7 +165,7 @@ def test_flux_two_shards_equal_one_batch():
     nx, nt, K, B = 33, 40, 5, 10
     uh, g = synthetic.gen_burgers_flux(105, B, nx, nt)
     p = Problem("E", nx, nt, n_flux=K)
-    u, lam, st, _, _ = H.run_gpu(p, uh, g)
+    u, lam, st, _ = H.run_gpu(p, uh, g)
     parts = [H.run_gpu(p, uh[s], g[s]) for s in (slice(0, 3), slice(3, B))]
     np.testing.assert_array_equal(np.concatenate([q[0] for q in parts]), u)
     np.testing.assert_array_equal(np.concatenate([q[1] for q in parts]), lam)

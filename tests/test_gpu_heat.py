@@ -28,7 +28,7 @@ def _assert_lam(nx, nt, lam, le):
 
 def _run(nx, nt, uh, pr):
     p = Problem("F", nx, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     return p, u, lam, st, d
 
 

@@ -16,7 +16,7 @@ FLOOR = -1e300
 def test_vorticity_against_dense_oracle(N, nt, B, seed):
     uh, pr = synthetic.gen_vorticity(seed, B, N, nt)
     p = vorticity_problem(N, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= H.H_TOL
     ue, le, so, S, _ = solve.project_1d("A", N * N, nt, pr, uh, energy_floor=FLOOR)
     assert (so["status"] == 0).all()
@@ -30,7 +30,7 @@ def test_vorticity_full_size_closed_form_and_conservation():
     B, N, nt = w["B"], w["N"], w["nt"]
     uh, pr = synthetic.gen_vorticity(w["seed"], B, N, nt)
     p = vorticity_problem(N, nt)
-    u, lam, st, _, d = H.run_gpu(p, uh, pr)
+    u, lam, st, d = H.run_gpu(p, uh, pr)
     assert (st["status"] == 0).all() and st["h_inf"].max() <= H.H_TOL
     ue, le = pins_1d.family_a_closed_form(N * N, nt, pr, uh, energy_floor=FLOOR)
     H.assert_u_close(u, ue)

@@ -25,7 +25,7 @@ def _noalloc(p, uh, pr, **opt):
 
 def _compare(p, uh, pr, **opt):
     u1, l1, s1 = _noalloc(p, uh, pr, **opt)
-    u0, l0, s0, _ = p.project(uh, pr, opts=options(**opt))
+    u0, l0, s0 = p.project(uh, pr, opts=options(**opt))
     torch.cuda.synchronize()
     s0 = decode_stats(s0)
     np.testing.assert_array_equal(s1["status"], s0["status"])
