@@ -641,6 +641,7 @@ def measure_uneven(dev, reps=30):
         g["pr"].copy_(torch.as_tensor(np.stack([mix[i]["params"] for i in g["ids"]])))
         in_bytes += g["uh"].numel() * 8
     sched, tune_ms = b.autotune(reps=5)
+    group_lanes = {f"{f} {nx}x{nt}": l for (f, nx, nt), l in zip(keys, b.group_lanes())}
     n = len(mix)
     t_ns = torch.zeros(n, 2, dtype=torch.int64, device=dev)
     b.capture_graph(t_ns=t_ns)
@@ -688,7 +689,8 @@ def measure_uneven(dev, reps=30):
     gbw.replay()
     bms_g = _event_ms(gbw.replay, reps)
     return {"workload": "uneven", "instances": n, "groups": len(keys),
-            "schedule": sched, "autotune_best_ms": tune_ms,
+            "schedule": sched, "lanes_per_slice_by_group": group_lanes,
+            "autotune_best_ms": tune_ms,
             "persistent_ms_per_call": ms_p, "grouped_ms_per_call": ms_g,
             "speedup_vs_grouped": ms_g / ms_p,
             "converged_persistent": conv_p, "converged_grouped": conv_g,

@@ -380,7 +380,18 @@ typedef struct {
   int pack_1d;       /* 1: a 1-D tile's 32 slices may span consecutive instances of a group;
                         0: tiles end at instance boundaries */
   int sort_1d;       /* 1-D groups in the queue: 0 creation order, 1 widest grid (nx) first */
+  int tile_1d;       /* slices per 1-D work item: 16, 32 or 64 (a 64-slice item is two
+                        32-slice tiles run by the same warp) */
+  int lanes_1d;      /* lanes per slice of the 1-D load and write-back passes (2, 4 or 8) set
+                        for every 1-D group; 0 keeps each group's own value (forward kernel;
+                        the adjoint uses 4) */
 } snap_batch_schedule;
+
+/* Per-group lanes per slice (groups in problem order, n_groups entries as snap_batch_info
+ * reports; 2-D groups read 0 and ignore what is set).  Set: each 1-D entry 2, 4 or 8, else
+ * INVALID_ARG.  Host only, synchronous (uploads the group table). */
+SNAP_API snap_status snap_batch_get_group_lanes(snap_batch_t b, int *lanes);
+SNAP_API snap_status snap_batch_set_group_lanes(snap_batch_t b, const int *lanes);
 
 /* Host arrays probs[n_problems], inst_problem[n_inst]; the problems must outlive the batch.
  * Allocates the batch's device tables on the current device (bind and project use it).
@@ -424,8 +435,12 @@ SNAP_API snap_status snap_batch_get_schedule(snap_batch_t b, snap_batch_schedule
 SNAP_API snap_status snap_batch_set_schedule(snap_batch_t b, const snap_batch_schedule *s);
 
 /* Autotuner: times snap_batch_project (CUDA events on stream, `reps` launches after one
- * warm-up, best of them) for every schedule of the search space, keeps the fastest on the
- * batch and returns it in *best (and its time in *best_ms, either may be NULL).  Runs the
+ * warm-up, best of them) over the search space in three stages -- the 16 combinations of
+ * ctas_per_sm, order, pack_1d and sort_1d (32-slice items, 4 lanes per slice); then tile_1d
+ * in {16, 32, 64}; then, one 1-D group at a time, its lanes per slice in {2, 4, 8} --, keeps
+ * the fastest on the batch and returns it in *best (lanes_1d = 0: the chosen per-group values
+ * are in the batch, snap_batch_get_group_lanes) and its time in *best_ms (either may be
+ * NULL).  Runs the
  * projection on the bound buffers (outputs are overwritten with the same results);
  * synchronous.  Errors: as snap_batch_project. */
 SNAP_API snap_status snap_batch_autotune(snap_batch_t b, const snap_options *opt, void *workspace,

@@ -41,7 +41,7 @@ class Options(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("ctas_per_sm", C.c_int), ("order", C.c_int), ("pack_1d", C.c_int),
-                ("sort_1d", C.c_int)]
+                ("sort_1d", C.c_int), ("tile_1d", C.c_int), ("lanes_1d", C.c_int)]
 
 
 assert C.sizeof(Stats) == 40
@@ -79,6 +79,8 @@ _PROTOS = {
     "snap_batch_project": (C.c_int, [_vp, C.POINTER(Options), _vp, _vp, C.c_size_t, _vp]),
     "snap_batch_project_grouped": (C.c_int, [_vp, C.POINTER(Options), _vp, C.c_size_t, _vp]),
     "snap_batch_get_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
+    "snap_batch_get_group_lanes": (C.c_int, [_vp, _ip]),
+    "snap_batch_set_group_lanes": (C.c_int, [_vp, _ip]),
     "snap_batch_set_schedule": (C.c_int, [_vp, C.POINTER(Schedule)]),
     "snap_batch_autotune": (C.c_int, [_vp, C.POINTER(Options), _vp, C.c_size_t, _vp, C.c_int,
                                       C.POINTER(Schedule), _dp]),

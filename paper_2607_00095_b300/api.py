@@ -249,7 +249,8 @@ class SnapProject(torch.autograd.Function):
 
 
 def _schedule_dict(s):
-    return dict(ctas_per_sm=s.ctas_per_sm, order=s.order, pack_1d=s.pack_1d, sort_1d=s.sort_1d)
+    return dict(ctas_per_sm=s.ctas_per_sm, order=s.order, pack_1d=s.pack_1d, sort_1d=s.sort_1d,
+                tile_1d=s.tile_1d, lanes_1d=s.lanes_1d)
 
 
 class Batch:
@@ -347,8 +348,20 @@ class Batch:
     def set_schedule(self, **kw):
         d = self.schedule()
         d.update(kw)
-        s = _abi.Schedule(d["ctas_per_sm"], d["order"], d["pack_1d"], d["sort_1d"])
+        s = _abi.Schedule(d["ctas_per_sm"], d["order"], d["pack_1d"], d["sort_1d"], d["tile_1d"],
+                          d.get("lanes_1d", 0))
         check(lib().snap_batch_set_schedule(self._h, C.byref(s)))
+
+    def group_lanes(self):
+        """Lanes per slice of every group (problem order; 0 for 2-D groups)."""
+        n = self.info()["groups"]
+        a = np.zeros(max(n, 1), np.int32)
+        check(lib().snap_batch_get_group_lanes(self._h, a.ctypes.data_as(C.POINTER(C.c_int))))
+        return a[:n].tolist()
+
+    def set_group_lanes(self, lanes):
+        a = np.ascontiguousarray(lanes, dtype=np.int32)
+        check(lib().snap_batch_set_group_lanes(self._h, a.ctypes.data_as(C.POINTER(C.c_int))))
 
     def autotune(self, opts=None, reps=3, stream=None):
         """Time every schedule, keep the fastest; returns (schedule dict, ms)."""

@@ -52,6 +52,7 @@ struct GroupRec {
   long long bst_off;        // first statistics record of the group in the workspace
   int kind;                 // 0: 1-D, 1: 2-D
   int n_inst, list_off, nt, M;
+  int lps;                  // 1-D: lanes per slice in the load / write-back passes (2, 4, 8)
 };
 
 struct Item1D { int group, s0, s1; };     // slices [s0, s1) of the group's virtual batch
@@ -220,6 +221,40 @@ __device__ __noinline__ void finish_tile(const BatchArgs &a, unsigned it, int la
   }
 }
 
+// One 32-slice (or shorter) tile [t0, t1) of an item: the warp's context, then the tile with
+// the group's lanes per slice.
+__device__ __forceinline__ void run_subtile_1d(const BatchArgs &a, const GroupRec &G, int t0,
+                                               int t1, SampleDerived *sdw, TileCtx *cx) {
+  const int lane = threadIdx.x & 31;
+  const int nt = G.nt;
+  const int i0 = t0 / nt, i1 = (t1 - 1) / nt;
+  if (a.t_ns && lane <= i1 - i0) atomicMax(&a.negstart[a.list[G.list_off + i0 + lane]], ~gtimer());
+  {
+    const int *src = reinterpret_cast<const int *>(&G.g);
+    int *dst = reinterpret_cast<int *>(&cx->g);
+    if (lane < (int)(sizeof(Geom1D) / sizeof(int))) dst[lane] = src[lane];
+  }
+  if (lane == 0) {
+    cx->bst = a.bst + G.bst_off;
+    cx->nt = nt;
+    cx->nx = G.g.nx;
+    cx->list_off = G.list_off;
+    cx->first_inst = i0;
+  }
+  __syncwarp();
+  BatchTiles ad;
+  ad.inst = a.inst;
+  ad.list = a.list;
+  ad.sdw = sdw;
+  ad.c = cx;
+  ad.tol_kkt = a.o.tol_kkt;
+  const SliceOptsT<float> so_f = slice_opts<float>(a.o, a.o.tol_kkt);
+  const SliceOptsT<df64> so_d = slice_opts<df64>(a.o, a.o.tol_kkt);
+  mixed_tile(cx->g, ad, t0, t1, a.o, so_f, so_d, df64(cx->g.dx),
+             G.lps == 2 ? 1 : (G.lps == 8 ? 3 : 2));
+  __syncwarp();                          // the context is rewritten by the next tile
+}
+
 __device__ __forceinline__ void batch_1d(const BatchArgs &a, SampleDerived *sdw, TileCtx *cx) {
   const int lane = threadIdx.x & 31;
   for (;;) {
@@ -229,36 +264,16 @@ __device__ __forceinline__ void batch_1d(const BatchArgs &a, SampleDerived *sdw,
     if (it >= (unsigned)a.n1d) break;
     const Item1D w = a.items1d[it];
     const GroupRec &G = a.groups[w.group];
-    const int nt = G.nt;
-    const int i0 = w.s0 / nt, i1 = (w.s1 - 1) / nt;
-    if (a.t_ns && lane <= i1 - i0) atomicMax(&a.negstart[a.list[G.list_off + i0 + lane]], ~gtimer());
-    {
-      const int *src = reinterpret_cast<const int *>(&G.g);
-      int *dst = reinterpret_cast<int *>(&cx->g);
-      if (lane < (int)(sizeof(Geom1D) / sizeof(int))) dst[lane] = src[lane];
+    // an item of up to 64 slices runs as tiles of at most 32
+    for (int t0 = w.s0; t0 < w.s1; t0 += 32) {
+      const int t1 = (t0 + 32 < w.s1) ? t0 + 32 : w.s1;
+      run_subtile_1d(a, G, t0, t1, sdw, cx);
     }
-    if (lane == 0) {
-      cx->bst = a.bst + G.bst_off;
-      cx->nt = nt;
-      cx->nx = G.g.nx;
-      cx->list_off = G.list_off;
-      cx->first_inst = i0;
-    }
-    __syncwarp();
-    BatchTiles ad;
-    ad.inst = a.inst;
-    ad.list = a.list;
-    ad.sdw = sdw;
-    ad.c = cx;
-    ad.tol_kkt = a.o.tol_kkt;
-    const SliceOptsT<float> so_f = slice_opts<float>(a.o, a.o.tol_kkt);
-    const SliceOptsT<df64> so_d = slice_opts<df64>(a.o, a.o.tol_kkt);
-    mixed_tile(cx->g, ad, w.s0, w.s1, a.o, so_f, so_d, df64(cx->g.dx));
     // arrival: every lane's statistics and outputs are fenced before lane 0 counts
     __threadfence();
     __syncwarp();
     finish_tile(a, it, lane);
-    __syncwarp();                        // the context is rewritten by the next tile
+    __syncwarp();
   }
 }
 
@@ -409,8 +424,7 @@ __device__ __forceinline__ void batch_2d_bwd(const BwdArgs &a, unsigned char *sm
 
 // Arrival of adjoint tile `it`: count its slices per instance; the last arrival forms the
 // instance's dL/dparams.
-__device__ __noinline__ void finish_tile_bwd(const BwdArgs &a, unsigned it, int lane,
-                                             const SampleDerived *sdw, int first_inst) {
+__device__ __noinline__ void finish_tile_bwd(const BwdArgs &a, unsigned it, int lane) {
   const Item1D w = a.items1d[it];
   const GroupRec &G = a.groups[w.group];
   const int nt = G.nt;
@@ -429,7 +443,8 @@ __device__ __noinline__ void finish_tile_bwd(const BwdArgs &a, unsigned it, int 
     if (last && W.gp) {
       __threadfence();
       const InstRec &R = a.inst[id];
-      s1_param_grad<true>(G.g, W.gu, R.params, sdw[i - first_inst].M,
+      const double M = s1_derive(G.g, R.params, lane).M;
+      s1_param_grad<true>(G.g, W.gu, R.params, M,
                           a.contrib + G.bst_off + (long long)i * nt,
                           R.stats->status != SNAP_SAMPLE_OK, W.gp, lane);
     }
@@ -446,34 +461,39 @@ __device__ __forceinline__ void batch_1d_bwd(const BwdArgs &a, SampleDerived *sd
     const Item1D w = a.items1d[it];
     const GroupRec &G = a.groups[w.group];
     const int nt = G.nt;
-    const int i0 = w.s0 / nt;
-    {
-      const int *src = reinterpret_cast<const int *>(&G.g);
-      int *dst = reinterpret_cast<int *>(&cx->g);
-      if (lane < (int)(sizeof(Geom1D) / sizeof(int))) dst[lane] = src[lane];
+    // an item of up to 64 slices runs as tiles of at most 32
+    for (int t0 = w.s0; t0 < w.s1; t0 += 32) {
+      const int t1 = (t0 + 32 < w.s1) ? t0 + 32 : w.s1;
+      const int first = t0 / nt;
+      {
+        const int *src = reinterpret_cast<const int *>(&G.g);
+        int *dst = reinterpret_cast<int *>(&cx->g);
+        if (lane < (int)(sizeof(Geom1D) / sizeof(int))) dst[lane] = src[lane];
+      }
+      if (lane == 0) {
+        cx->nt = nt;
+        cx->nx = G.g.nx;
+        cx->list_off = G.list_off;
+        cx->first_inst = first;
+      }
+      __syncwarp();
+      BatchBwdTiles ad;
+      ad.inst = a.inst;
+      ad.bwd = a.bwd;
+      ad.list = a.list;
+      ad.contrib = a.contrib + G.bst_off;
+      ad.sdw = sdw;
+      ad.c = cx;
+      ad.s0 = t0;
+      ad.s1 = t1;
+      bwd_tile(cx->g, ad, t0);
+      __syncwarp();
     }
-    if (lane == 0) {
-      cx->nt = nt;
-      cx->nx = G.g.nx;
-      cx->list_off = G.list_off;
-      cx->first_inst = i0;
-    }
-    __syncwarp();
-    BatchBwdTiles ad;
-    ad.inst = a.inst;
-    ad.bwd = a.bwd;
-    ad.list = a.list;
-    ad.contrib = a.contrib + G.bst_off;
-    ad.sdw = sdw;
-    ad.c = cx;
-    ad.s0 = w.s0;
-    ad.s1 = w.s1;
-    bwd_tile(cx->g, ad, w.s0);
     // arrival: every lane's contributions and outputs are fenced before lane 0 counts
     __threadfence();
     __syncwarp();
-    finish_tile_bwd(a, it, lane, sdw, i0);
-    __syncwarp();                        // the context is rewritten by the next tile
+    finish_tile_bwd(a, it, lane);
+    __syncwarp();                        // the context is rewritten by the next item
   }
 }
 
@@ -517,7 +537,7 @@ struct snap_batch {
   bool bound = false;
   std::vector<InstRec> h_inst;
   std::vector<char> group_contig;        // bound buffers contiguous per group
-  snap_batch_schedule sched{2, 0, 1, 1};
+  snap_batch_schedule sched{2, 0, 1, 1, 32, 4};
   int n1d = 0, n2d = 0;
   int device = 0;
   int grid = 0;                          // persistent grid of the current schedule
@@ -566,12 +586,13 @@ void build_items(const snap_batch *b, const snap_batch_schedule &s, std::vector<
     const GroupRec &G = b->groups[gi];
     if (G.kind == 0) {
       const int total = G.n_inst * G.nt;
+      const int tile = s.tile_1d;
       if (s.pack_1d) {
-        for (int s0 = 0; s0 < total; s0 += 32) i1.push_back(Item1D{gi, s0, std::min(s0 + 32, total)});
+        for (int s0 = 0; s0 < total; s0 += tile) i1.push_back(Item1D{gi, s0, std::min(s0 + tile, total)});
       } else {
         for (int i = 0; i < G.n_inst; ++i)
-          for (int k = 0; k < G.nt; k += 32)
-            i1.push_back(Item1D{gi, i * G.nt + k, i * G.nt + std::min(k + 32, G.nt)});
+          for (int k = 0; k < G.nt; k += tile)
+            i1.push_back(Item1D{gi, i * G.nt + k, i * G.nt + std::min(k + tile, G.nt)});
       }
     }
   }
@@ -653,6 +674,21 @@ snap_status get_opts(const snap_options *opt, snap_options &o) {
   snap_options_default(&o);
   if (opt) o = *opt;
   if (snap_check_options(o) != SNAP_OK) return SNAP_ERR_INVALID_ARG;
+  return SNAP_OK;
+}
+
+// Lanes per slice of every 1-D group (2, 4 or 8; entries of 2-D groups ignored); uploads the
+// group table.
+snap_status set_group_lanes(snap_batch *b, const int *lanes) {
+  for (size_t k = 0; k < b->groups.size(); ++k)
+    if (b->groups[k].kind == 0 && lanes[k] != 2 && lanes[k] != 4 && lanes[k] != 8)
+      return snap_fail_msg(SNAP_ERR_INVALID_ARG, "lanes per slice must be 2, 4 or 8");
+  for (size_t k = 0; k < b->groups.size(); ++k)
+    if (b->groups[k].kind == 0) b->groups[k].lps = lanes[k];
+  if (!b->groups.empty() && cudaMemcpy(b->d_groups, b->groups.data(),
+                                       sizeof(GroupRec) * b->groups.size(),
+                                       cudaMemcpyHostToDevice) != cudaSuccess)
+    return snap_fail_msg(SNAP_ERR_CUDA, "upload of the group table failed");
   return SNAP_OK;
 }
 
@@ -791,8 +827,10 @@ SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *pro
     } else {
       G.kind = 0;
       G.g = p->g1;
-      cap1_packed += ((size_t)G.n_inst * G.nt + 31) / 32;
-      cap1_split += (size_t)G.n_inst * ((G.nt + 31) / 32);
+      // the smallest item size (16 slices) gives the most items
+      cap1_packed += ((size_t)G.n_inst * G.nt + 15) / 16;
+      cap1_split += (size_t)G.n_inst * ((G.nt + 15) / 16);
+      G.lps = 4;
     }
     const size_t wsg = (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) ? ws_bytes_2d(p, G.n_inst)
                                                                      : ws_bytes_1d(p, G.n_inst);
@@ -945,13 +983,33 @@ SNAP_API snap_status snap_batch_get_schedule(snap_batch_t b, snap_batch_schedule
 SNAP_API snap_status snap_batch_set_schedule(snap_batch_t b, const snap_batch_schedule *s) {
   if (!b || !s) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null argument");
   if (s->ctas_per_sm < 1 || s->ctas_per_sm > 2 || s->order < 0 || s->order > 1 ||
-      s->pack_1d < 0 || s->pack_1d > 1 || s->sort_1d < 0 || s->sort_1d > 1)
+      s->pack_1d < 0 || s->pack_1d > 1 || s->sort_1d < 0 || s->sort_1d > 1 ||
+      (s->tile_1d != 16 && s->tile_1d != 32 && s->tile_1d != 64) ||
+      (s->lanes_1d != 0 && s->lanes_1d != 2 && s->lanes_1d != 4 && s->lanes_1d != 8))
     return snap_fail_msg(SNAP_ERR_INVALID_ARG, "schedule field out of range");
+  if (s->lanes_1d != 0) {
+    std::vector<int> lanes(b->groups.size());
+    for (size_t k = 0; k < lanes.size(); ++k) lanes[k] = b->groups[k].kind == 0 ? s->lanes_1d : 0;
+    const snap_status st = set_group_lanes(b, lanes.data());
+    if (st != SNAP_OK) return st;
+  }
   const snap_batch_schedule old = b->sched;
   b->sched = *s;
   const snap_status st = upload_items(b);
   if (st != SNAP_OK) b->sched = old;
   return st;
+}
+
+SNAP_API snap_status snap_batch_get_group_lanes(snap_batch_t b, int *lanes) {
+  if (!b || !lanes) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null argument");
+  for (size_t k = 0; k < b->groups.size(); ++k)
+    lanes[k] = b->groups[k].kind == 0 ? b->groups[k].lps : 0;
+  return SNAP_OK;
+}
+
+SNAP_API snap_status snap_batch_set_group_lanes(snap_batch_t b, const int *lanes) {
+  if (!b || !lanes) return snap_fail_msg(SNAP_ERR_INVALID_ARG, "null argument");
+  return set_group_lanes(b, lanes);
 }
 
 SNAP_API snap_status snap_batch_autotune(snap_batch_t b, const snap_options *opt, void *workspace,
@@ -968,39 +1026,78 @@ SNAP_API snap_status snap_batch_autotune(snap_batch_t b, const snap_options *opt
     cudaEventDestroy(e0);
     return snap_fail_msg(SNAP_ERR_CUDA, "event create");
   }
+  // best of `reps` timed launches of the batch as it is now set up (after one warm-up)
+  auto time_now = [&](double &t) -> snap_status {
+    snap_status st = launch_batch(b, o, nullptr, workspace, workspace_bytes, s);
+    t = 1e300;
+    for (int r = 0; r < reps && st == SNAP_OK; ++r) {
+      cudaEventRecord(e0, s);
+      st = launch_batch(b, o, nullptr, workspace, workspace_bytes, s);
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess)
+        return snap_fail_msg(SNAP_ERR_CUDA, "autotune timing failed");
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      t = std::min(t, (double)ms);
+    }
+    return st;
+  };
+  const size_t ng = b->groups.size();
+  std::vector<int> lanes(ng), best_lanes(ng);
+  for (size_t k = 0; k < ng; ++k) lanes[k] = b->groups[k].kind == 0 ? 4 : 0;
+  snap_status st = set_group_lanes(b, lanes.data());
+  best_lanes = lanes;
   snap_batch_schedule bestS = b->sched;
   double bestT = 1e300;
-  snap_status st = SNAP_OK;
+  // stage 1: queue order and occupancy (32-slice items, 4 lanes per slice)
   for (int cps = 1; cps <= 2 && st == SNAP_OK; ++cps)
     for (int order = 0; order <= 1 && st == SNAP_OK; ++order)
       for (int pack = 0; pack <= 1 && st == SNAP_OK; ++pack)
         for (int sort = 0; sort <= 1 && st == SNAP_OK; ++sort) {
-          const snap_batch_schedule cand{cps, order, pack, sort};
+          const snap_batch_schedule cand{cps, order, pack, sort, 32, 0};
           st = snap_batch_set_schedule(b, &cand);
-          if (st != SNAP_OK) break;
-          st = launch_batch(b, o, nullptr, workspace, workspace_bytes, s);
           double t = 1e300;
-          for (int r = 0; r < reps && st == SNAP_OK; ++r) {
-            cudaEventRecord(e0, s);
-            st = launch_batch(b, o, nullptr, workspace, workspace_bytes, s);
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-              st = snap_fail_msg(SNAP_ERR_CUDA, "autotune timing failed");
-              break;
-            }
-            float ms = 0.0f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            t = std::min(t, (double)ms);
-          }
+          if (st == SNAP_OK) st = time_now(t);
           if (st == SNAP_OK && t < bestT) {
             bestT = t;
             bestS = cand;
           }
         }
+  // stage 2: slices per 1-D item
+  for (int tile : {16, 64}) {
+    if (st != SNAP_OK) break;
+    snap_batch_schedule cand = bestS;
+    cand.tile_1d = tile;
+    st = snap_batch_set_schedule(b, &cand);
+    double t = 1e300;
+    if (st == SNAP_OK) st = time_now(t);
+    if (st == SNAP_OK && t < bestT) {
+      bestT = t;
+      bestS = cand;
+    }
+  }
+  if (st == SNAP_OK) st = snap_batch_set_schedule(b, &bestS);
+  // stage 3: lanes per slice, one 1-D group at a time (coordinate descent from 4)
+  for (size_t k = 0; k < ng && st == SNAP_OK; ++k) {
+    if (b->groups[k].kind != 0) continue;
+    for (int l : {2, 8}) {
+      lanes = best_lanes;
+      lanes[k] = l;
+      st = set_group_lanes(b, lanes.data());
+      double t = 1e300;
+      if (st == SNAP_OK) st = time_now(t);
+      if (st != SNAP_OK) break;
+      if (t < bestT) {
+        bestT = t;
+        best_lanes = lanes;
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != SNAP_OK) return st;
   st = snap_batch_set_schedule(b, &bestS);
+  if (st == SNAP_OK) st = set_group_lanes(b, best_lanes.data());
   if (st != SNAP_OK) return st;
   if (best) *best = bestS;
   if (best_ms) *best_ms = bestT;

@@ -4,21 +4,20 @@
 // pointer set per instance); it is the tile of the per-problem kernel k1d_mixed
 // (kern_1d_mixed.cu), which keeps the same phases inline in its grid-stride loop for speed.
 //
-//   phase 1  (4 lanes per slice, 8 slices per warp instruction, 16-byte loads): every
-//            u_hat_i is split into a float pair hi + lo with integer operations and one
-//            conversion (|u_hat - hi - lo| <= 2^-48 |u_hat|), and the interior moments
+//   phase 1  (LPS = 2, 4 or 8 lanes per slice, 32 / LPS slices per warp instruction, 16-byte
+//            loads): every u_hat_i is split into a float pair hi + lo with integer operations
+//            only (|u_hat - hi - lo| < 2^-46 |u_hat|), and the interior moments
 //            S1 = sum u_hat_i, S2 = sum u_hat_i^2 are accumulated in double-float
-//            (error-free TwoSum / TwoProd), reduced across the 4 lanes with two butterfly
-//            steps;
+//            (error-free TwoSum / TwoProd), reduced across the LPS lanes by butterfly steps;
 //   phase 2  (one slice per lane): the slice's Newton-KKT iteration in moment form,
 //            first in float, then in double-float to the FP64 stopping tolerance
 //            (slice_solve_mixed); E_k = E0 q^k with q = exp(-r dt) by binary powering in
 //            double-float;
-//   phase 3  (4 lanes per slice): u = fma(a, u_hat, c) in FP64, 16-byte stores.
+//   phase 3  (LPS lanes per slice): u = fma(a, u_hat, c) in FP64, 16-byte stores.
 //
 // Slice k = 0 (the IC block) is skipped: the caller solves it (s1_ic_forward).  A slice whose
-// values leave the range of the float-pair representation (|u_hat| outside [2^-74, 2^57], or
-// non-finite) falls back to FP64 moments and the FP64 iteration.
+// values leave the range of the float-pair representation (|u_hat| outside [2^-74, 2^57], exactly
+// zero, or non-finite) falls back to FP64 moments and the FP64 iteration.
 //
 // u_hat and the parameters are read through the read-only path (__ldg): the kernel never
 // writes them.
@@ -186,14 +185,20 @@ __device__ __forceinline__ void t1_solve_slice(
   *stat = st;
 }
 
+// LPS = 2^lps_log2 lanes per slice in phases 1 and 3 (2, 4 or 8; a runtime value, so that one
+// instance of the tile serves every group): 32 / LPS slices per round, LPS rounds.  A different
+// LPS sums the moments in a different order (results agree to rounding).
 template <class Addr>
 __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long long sbase,
                                            long long send, const SolverOpts &o,
                                            const SliceOptsT<float> &so_f,
-                                           const SliceOptsT<df64> &so_d, const df64 &dxd) {
+                                           const SliceOptsT<df64> &so_d, const df64 &dxd,
+                                           int lps_log2) {
+  const int LPS = 1 << lps_log2;
+  const int SPR = 32 >> lps_log2;   // slices per round
   const int lane = threadIdx.x & 31;
-  const int q = lane >> 2;        // group: slice 8*rho + q of round rho
-  const int r = lane & 3;         // lane within the group
+  const int q = lane >> lps_log2;   // group: slice SPR*rho + q of round rho
+  const int r = lane & (LPS - 1);   // lane within the group
   const int nx = g.nx, ih = g.ih;
   // ---------------- phase 1 ----------------
   ad.prefetch(sbase, send, lane);
@@ -201,8 +206,8 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
   float mmx = -INFINITY, mmn = INFINITY;
   int mok = 1;
 #pragma unroll 1
-  for (int rho = 0; rho < 4; ++rho) {
-    const long long s = sbase + 8 * rho + q;
+  for (int rho = 0; rho < LPS; ++rho) {
+    const long long s = sbase + SPR * rho + q;
     float s1h = 0.0f, s1e = 0.0f, s2h = 0.0f, s2e = 0.0f;
     float pmx = -INFINITY, pmn = INFINITY;
     int ok = 1;
@@ -214,20 +219,20 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
       } else {
         // CH independent 16-byte loads in flight per lane, then the accumulation
         constexpr int CH = 8;
-        for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
+        for (int i0 = 2 * r; i0 < nx; i0 += 2 * LPS * CH) {
           double2 v[CH];
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
+            const int i = i0 + 2 * LPS * c;
             v[c] = (i < nx) ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
           }
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
+            const int i = i0 + 2 * LPS * c;
             if (i >= nx) break;
             float h0, l0, h1, l1;
-            ok &= df_split(v[c].x, h0, l0);
-            ok &= df_split(v[c].y, h1, l1);
+            ok &= df_split_trunc_fast(v[c].x, h0, l0);
+            ok &= df_split_trunc_fast(v[c].y, h1, l1);
             if (i == 0 || i == ih) { h0 = 0.0f; l0 = 0.0f; }
             if (i + 1 == ih) { h1 = 0.0f; l1 = 0.0f; }
             else { pmx = fmaxf(pmx, h1); pmn = fminf(pmn, h1); }
@@ -263,7 +268,7 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
     df64 a1 = df_fast_two_sum(s1h, s1e);
     df64 a2 = df_fast_two_sum(s2h, s2e);
 #pragma unroll
-    for (int off = 1; off < 4; off <<= 1) {
+    for (int off = 1; off < LPS; off <<= 1) {
       a1 = a1 + t1_shfl_df(a1, off);
       a2 = a2 + t1_shfl_df(a2, off);
       pmx = fmaxf(pmx, __shfl_xor_sync(0xffffffffu, pmx, off));
@@ -276,7 +281,7 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
   }
   ad.before_solve(sbase, send, lane);
   // ---------------- phase 2: one slice per lane ----------------
-  const long long s = sbase + 8 * r + q;
+  const long long s = sbase + SPR * r + q;
   int kind = T1_KIND_NONE;
   double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
   if (s < send) {
@@ -289,31 +294,31 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
                      so_d, dxd, A, Cc, P0, PH);
     }
   }
-  // ---------------- phase 3: write-back, 4 lanes per slice ----------------
+  // ---------------- phase 3: write-back, LPS lanes per slice ----------------
 #pragma unroll 1
-  for (int rho = 0; rho < 4; ++rho) {
-    const int src = 4 * q + rho;
+  for (int rho = 0; rho < LPS; ++rho) {
+    const int src = LPS * q + rho;
     const double a = __shfl_sync(0xffffffffu, A, src);
     const double c0 = __shfl_sync(0xffffffffu, Cc, src);
     const double p0 = __shfl_sync(0xffffffffu, P0, src);
     const double ph = __shfl_sync(0xffffffffu, PH, src);
     const int kd = __shfl_sync(0xffffffffu, kind, src);
-    const long long s2 = sbase + 8 * rho + q;
+    const long long s2 = sbase + SPR * rho + q;
     if (s2 >= send || kd == T1_KIND_NONE) continue;
     const double *row = ad.row_in(s2);
     double *out = ad.row_out(s2);
     if (kd == T1_KIND_MOMENT) {
       constexpr int CH = 8;
-      for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
+      for (int i0 = 2 * r; i0 < nx; i0 += 2 * LPS * CH) {
         double2 v[CH];
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-          const int i = i0 + 8 * c;
+          const int i = i0 + 2 * LPS * c;
           v[c] = (i < nx) ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
         }
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-          const int i = i0 + 8 * c;
+          const int i = i0 + 2 * LPS * c;
           if (i >= nx) break;
           double2 w;
           w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v[c].x, c0));

@@ -125,6 +125,43 @@ def test_batch_matches_per_group_project_every_schedule():
     _assert_same(_outputs(bufs), ref)
 
 
+def test_batch_tile_shapes():
+    """Slices per 1-D item (16, 32, 64) do not change a slice's arithmetic: the same bits.
+    Lanes per slice (2, 4, 8, for all groups or per group) sum the moments in a different
+    order: the same point to rounding."""
+    specs, probs, inst, data = _small_mix(10)
+    b = Batch(probs, inst)
+    bufs = b.alloc("cuda:0")
+    _fill(b, bufs, data)
+    b.set_schedule(tile_1d=32, lanes_1d=4)
+    b.project()
+    torch.cuda.synchronize()
+    ref = _outputs(bufs)
+    for tile in (16, 64):
+        b.set_schedule(tile_1d=tile)
+        b.project()
+        torch.cuda.synchronize()
+        _assert_same(_outputs(bufs), ref)
+    b.set_schedule(tile_1d=32)
+    for lanes in (2, 8):
+        b.set_schedule(lanes_1d=lanes)
+        assert all(l == lanes for k, l in enumerate(b.group_lanes()) if specs[k][0] != "C")
+        b.project()
+        torch.cuda.synchronize()
+        _assert_close(_outputs(bufs), ref, probs)
+    mixed = [(2, 4, 8)[k % 3] if specs[k][0] != "C" else 0 for k in range(len(specs))]
+    b.set_group_lanes(mixed)
+    b.set_schedule(lanes_1d=0)
+    assert b.group_lanes() == mixed
+    b.project()
+    torch.cuda.synchronize()
+    _assert_close(_outputs(bufs), ref, probs)
+    with pytest.raises(_abi.SnapError):
+        b.set_schedule(tile_1d=48)
+    with pytest.raises(_abi.SnapError):
+        b.set_group_lanes([3] * len(specs))
+
+
 def test_batch_against_oracle():
     specs, probs, inst, data = _small_mix(8)
     b = Batch(probs, inst)
@@ -212,8 +249,12 @@ def test_graph_autotune_and_rebind():
     bufs = b.alloc("cuda:0")
     _fill(b, bufs, data)
     sch, ms = b.autotune(reps=2)
-    assert sch in SCHEDULES and ms > 0
+    base = {k: sch[k] for k in ("ctas_per_sm", "order", "pack_1d", "sort_1d")}
+    assert base in SCHEDULES and ms > 0
+    assert sch["tile_1d"] in (16, 32, 64) and sch["lanes_1d"] == 0
     assert b.schedule() == sch
+    lanes = b.group_lanes()
+    assert all((l in (2, 4, 8)) if specs[k][0] != "C" else l == 0 for k, l in enumerate(lanes))
     b.project()
     torch.cuda.synchronize()
     ref = _outputs(bufs)
