@@ -251,6 +251,12 @@ __device__ __forceinline__ void fd_mma(float (&c)[4], const uint32_t (&a)[4], ui
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+// Layout of the 32 x 32 operands of the tensor-core class solve (class arrays, Q, Q^T and the
+// eigenvalue scaling): element (row k, column m) at k 32 + (m ^ 8 (k & 3)).  The XOR moves the
+// four rows a fragment load touches (t = 0..3) to four different groups of eight banks, so the
+// fragment loads are conflict-free and the accumulator stores two-way instead of eight-way.
+__device__ __forceinline__ int fd_sw32(int k, int m) { return k * 32 + (m ^ (8 * (k & 3))); }
+
 // acc[nt][.] = the 16 x 8 output tiles (rows m0 .. m0 + 15, columns 8 nt ..) of X^T Y, M = 32
 __device__ __forceinline__ void fd_xty32(const float *X, const float *Y, int m0,
                                          float (&acc)[4][4]) {
@@ -262,8 +268,8 @@ __device__ __forceinline__ void fd_xty32(const float *X, const float *Y, int m0,
 #pragma unroll
   for (int k0 = 0; k0 < 32; k0 += 8) {
     // A = X^T: a0 (m0+g, k0+t), a1 (m0+g+8, k0+t), a2 (m0+g, k0+t+4), a3 (m0+g+8, k0+t+4)
-    const float af[4] = {X[(k0 + t) * 32 + m0 + g], X[(k0 + t) * 32 + m0 + g + 8],
-                         X[(k0 + t + 4) * 32 + m0 + g], X[(k0 + t + 4) * 32 + m0 + g + 8]};
+    const float af[4] = {X[fd_sw32(k0 + t, m0 + g)], X[fd_sw32(k0 + t, m0 + g + 8)],
+                         X[fd_sw32(k0 + t + 4, m0 + g)], X[fd_sw32(k0 + t + 4, m0 + g + 8)]};
     uint32_t ab[4], as[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -273,7 +279,7 @@ __device__ __forceinline__ void fd_xty32(const float *X, const float *Y, int m0,
 #pragma unroll
     for (int nt = 0; nt < 4; ++nt) {
       // B = Y: b0 (k0+t, 8 nt + g), b1 (k0+t+4, 8 nt + g)
-      const float y0 = Y[(k0 + t) * 32 + 8 * nt + g], y1 = Y[(k0 + t + 4) * 32 + 8 * nt + g];
+      const float y0 = Y[fd_sw32(k0 + t, 8 * nt + g)], y1 = Y[fd_sw32(k0 + t + 4, 8 * nt + g)];
       const uint32_t bb0 = fd_tf32(y0), bb1 = fd_tf32(y1);
       const uint32_t bs0 = fd_tf32(y0 - __uint_as_float(bb0));
       const uint32_t bs1 = fd_tf32(y1 - __uint_as_float(bb1));
@@ -295,9 +301,9 @@ __device__ __forceinline__ void fd_store32(float *out, const float (&acc)[4][4],
     for (int h = 0; h < 2; ++h) {
       const int m = m0 + g + 8 * h;
       float v0 = acc[nt][2 * h], v1 = acc[nt][2 * h + 1];
-      if (scale) { v0 *= scale[m * 32 + n]; v1 *= scale[m * 32 + n + 1]; }
-      out[m * 32 + n] = v0;
-      out[m * 32 + n + 1] = v1;
+      if (scale) { v0 *= scale[fd_sw32(m, n)]; v1 *= scale[fd_sw32(m, n + 1)]; }
+      out[fd_sw32(m, n)] = v0;
+      out[fd_sw32(m, n + 1)] = v1;
     }
   }
 }
@@ -446,6 +452,28 @@ struct View2D {
   __device__ df64 z(int slot) const { return df64(Zh[slot], Zl[slot]); }
 };
 
+// Position of class slot s (= c M^2 + q M + p) in the class work arrays r / t: the
+// tensor-core layout for M = 32, the plain one otherwise.
+template <int M>
+__device__ __forceinline__ int fd_slot(int s) {
+  if constexpr (M == 32) return (s & ~1023) + fd_sw32((s >> 5) & 31, s & 31);
+  else return s;
+}
+
+// The class eigenvectors Q, Q^T and the inverse eigenvalues into shared memory (row-major
+// M x M; the tensor-core layout for M = 32).
+template <int M>
+__device__ __forceinline__ void load_class_factor(View2D<M> &v, const float *__restrict__ Qg,
+                                                  const float *__restrict__ Ig) {
+  for (int i = threadIdx.x; i < M * M; i += T2D) {
+    const int k = i / M, m = i % M;
+    const float q = Qg[i];
+    v.Q[fd_slot<M>(i)] = q;
+    v.I[fd_slot<M>(i)] = Ig[i];
+    v.Qt[fd_slot<M>(m * M + k)] = q;
+  }
+}
+
 // Solve (D D^T) z = b on the four classes of one frame (b already in Bh/Bl), result in
 // Zh/Zl with z = 0 at each class's left-out cell.  REFINE float solves, the residual
 // r = b - (D D^T) z formed in double-float between them.
@@ -455,7 +483,7 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
   for (int s = threadIdx.x; s < NN; s += T2D) {
     v.Zh[s] = 0.0f;
     v.Zl[s] = 0.0f;
-    v.Rf[s] = v.Bh[s];
+    v.Rf[fd_slot<M>(s)] = v.Bh[s];
   }
   __syncthreads();
   // scale = 4 dx^2 and its inverse are powers of two (N is)
@@ -465,7 +493,7 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
     else if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
     else fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
     for (int s = threadIdx.x; s < NN; s += T2D) {
-      const df64 zz = df_add_fast(v.z(s), df64(v.Rf[s] * scale_f, 0.0f));
+      const df64 zz = df_add_fast(v.z(s), df64(v.Rf[fd_slot<M>(s)] * scale_f, 0.0f));
       v.Zh[s] = zz.hi;
       v.Zl[s] = zz.lo;
     }
@@ -481,7 +509,7 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
                                                  v.z(base + ((q + M - 1) % M) * M + p)));
         const df64 az = df_scale2(df_sub_fast(df_scale2(zc, 4.0f), nb), inv_scale_f);
         const df64 r = df_sub_fast(df64(v.Bh[s], v.Bl[s]), az);
-        v.Rf[s] = r.hi + r.lo;
+        v.Rf[fd_slot<M>(s)] = r.hi + r.lo;
       }
       __syncthreads();
     }
@@ -579,22 +607,20 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
                                 const float *__restrict__ Qg, const float *__restrict__ Ig,
                                 double *__restrict__ dst, double *__restrict__ lam_s,
                                 BlockStat *__restrict__ out, const SolverOpts &o) {
-  constexpr int N = 2 * M, NN = N * N, MM = M * M;
+  constexpr int N = 2 * M, NN = N * N;
   const df64 h2((float)N * 0.5f, 0.0f);          // 1 / (2 dx), exact
   const df64 dx(1.0 / N);
   const df64 scale = df64(4.0 / ((double)N * (double)N));   // 4 dx^2
-  for (int i = threadIdx.x; i < MM; i += T2D) {
-    v.Q[i] = Qg[i];
-    v.I[i] = Ig[i];
-    v.Qt[(i % M) * M + i / M] = Qg[i];
-  }
+  load_class_factor<M>(v, Qg, Ig);
   // w_hat as float pairs in the Poisson work area (z hi / lo, r, t: 4 N^2 floats = 2 N^2 pairs)
   float2 *xp = reinterpret_cast<float2 *>(v.Zh);
   df64 a0(0.0f, 0.0f);
+  float xinf = 0.0f;
   frame_elems<2 * NN>(src, [&](int e, double xd) {
     const df64 x = isplit(xd);
     xp[e] = make_float2(x.hi, x.lo);
     a0 = df_add_fast(a0, x * x);
+    xinf = fabs_max(xinf, x.hi);
   });
   __syncthreads();
   // b = D w_hat on every cell
@@ -612,25 +638,23 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   }
   __syncthreads();
   poisson_frame<M>(v, scale);
-  // y = D^T z, kept as float pairs in the right-hand-side and product areas (free after the
-  // solve; component 0 over b hi / lo, component 1 over r / t), and its moments.  The
-  // extremes are stopping-test bounds, formed from the leading parts.
-  float2 *y0 = reinterpret_cast<float2 *>(v.Bh), *y1 = reinterpret_cast<float2 *>(v.Rf);
+  // ||y||^2 = ||D^T z||^2 = z . (D D^T z) = z . b (D D^T z = b on every cell: the right-hand
+  // side of each class sums to zero), and the stopping-test extremes from bounds:
+  // |y_e| <= 2 h2 max |z|, |x_e - y_e| <= max |x| + that (looser bounds make the test stricter)
   df64 a2(0.0f, 0.0f);
-  float pinf = 0.0f, yinf = 0.0f;
-  frame_elems<2 * NN>(src, [&](int e, double xd) {
-    const df64 y = divT_at<M>(v, e, h2);
-    if (e < NN) y0[e] = make_float2(y.hi, y.lo); else y1[e - NN] = make_float2(y.hi, y.lo);
-    a2 = df_add_fast(a2, y * y);
-    yinf = fabs_max(yinf, y.hi);
-    pinf = fabs_max(pinf, isplit(xd).hi - y.hi);
-  });
+  float zinf = 0.0f;
+  for (int cell = threadIdx.x; cell < NN; cell += T2D) {
+    const df64 zc = v.z(cell);
+    a2 = df_add_fast(a2, zc * df64(v.Bh[cell], v.Bl[cell]));
+    zinf = fabs_max(zinf, zc.hi);
+  }
   a0 = block_sumdf(a0, v.red);
   a2 = block_sumdf(a2, v.red);
   d2 = block_sumf(d2, v.red);
   dinf = block_max(dinf, v.red);
-  pinf = block_max(pinf, v.red);
-  yinf = block_max(yinf, v.red);
+  xinf = block_max(xinf, v.red);
+  zinf = block_max(zinf, v.red);
+  const float yinf = 2.0f * h2.hi * zinf * (1.0f + 1e-6f), pinf = (xinf + yinf) * (1.0f + 1e-6f);
   // scalar Newton-KKT of the frame (thread 0), broadcast through shared memory
   __shared__ float zs[10];
   __shared__ SliceResult Rs;
@@ -666,8 +690,7 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
   const float pg = (AL * A - one).hi, rg = (AL * Cc + MU).hi;
   float ginf = 0.0f;
   frame_elems<2 * NN>(src, [&](int e, double xd) {
-    const float2 yp = (e < NN) ? y0[e] : y1[e - NN];
-    const df64 y(yp.x, yp.y);
+    const df64 y = divT_at<M>(v, e, h2);
     const df64 x = isplit(xd);
     const df64 w = df_add_fast(A * x, Cc * y);
     const double wd = df_to_double(w);
@@ -724,15 +747,11 @@ __device__ void frame2d_backward(View2D<M> &v, const double *__restrict__ gsrc,
                                  const double *__restrict__ pr, int f, int nt, bool bad,
                                  const float *__restrict__ Qg, const float *__restrict__ Ig,
                                  double *__restrict__ dst, BwdContrib *__restrict__ contrib) {
-  constexpr int N = 2 * M, NN = N * N, MM = M * M;
+  constexpr int N = 2 * M, NN = N * N;
   const df64 h2((float)N * 0.5f, 0.0f);
   const df64 dx(1.0 / N);
   const df64 scale = df64(4.0 / ((double)N * (double)N));
-  for (int i = threadIdx.x; i < MM; i += T2D) {
-    v.Q[i] = Qg[i];
-    v.I[i] = Ig[i];
-    v.Qt[(i % M) * M + i / M] = Qg[i];
-  }
+  load_class_factor<M>(v, Qg, Ig);
   // gbar as float pairs in the Poisson work area for the divergence stencil (as the forward)
   float2 *gp2 = reinterpret_cast<float2 *>(v.Zh);
   df64 dot(0.0f, 0.0f), ww(0.0f, 0.0f);
