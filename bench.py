@@ -39,7 +39,7 @@ KERNELS = ("k1d_mixed",)
 KERNEL = "+".join(KERNELS)
 KERNEL_SOURCES = ("paper_2607_00095_b300/csrc/kern_1d_mixed.cu", "paper_2607_00095_b300/csrc/tile_1d.cuh",
                   "paper_2607_00095_b300/csrc/slice_newton.cuh", "paper_2607_00095_b300/csrc/df64.cuh",
-                  "paper_2607_00095_b300/csrc/snap_internal.h")
+                  "paper_2607_00095_b300/csrc/snap_internal.h", "paper_2607_00095_b300/csrc/snap_bounds.cuh")
 
 
 def parse():
