@@ -26,6 +26,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "df64.cuh"
 #include "snap_bounds.cuh"
 #include "snap_internal.h"
 
@@ -220,12 +221,480 @@ __device__ __forceinline__ double heat_slice_residual(const HeatArgs &a, int k, 
   return h_nan_max(h_warp_max(mx), h_nan_max(fabs(hm), fabs(he)));
 }
 
-// Forward projection: u (time chain), lambda (backward substitution), statistics.
+// ---------------------------------------------------------------------------------------------
+// The time chains in double-float on the FP32 pipe (df64.cuh: ~48-bit significands), one warp per
+// sample.  The FP64 pipe of a B300 SM retires 2 lanes per clock against 128 FP32 lanes, and the
+// chains above are FP64-bound; here FP64 is left only for the conversion of the written u and
+// lambda to double (one addition per value).  The factor constants are formed in FP64 once per
+// sample and split.  The stored u and lambda are the double roundings of the double-float chain
+// values, so the residual of a Crank-Nicolson step is the local error of the double-float solve
+// (a few units of 2^-47 relative, times (1 + 4 kappa) / dt), far inside the FP64 stopping
+// tolerance, and the stored u agrees with the FP64 chain to ~1e-12 relative.
+
+// a b + c with one error-free transformation on the leading parts (the accuracy of df_add_fast)
+__device__ __forceinline__ df64 hd_fma(df64 a, df64 b, df64 c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const df64 s = df_two_sum(p, c.hi);
+  return df_fast_two_sum(s.hi, s.lo + (e + c.lo));
+}
+
+__device__ __forceinline__ df64 hd_shfl(df64 v, int src) {
+  return df64(__shfl_sync(kAll, v.hi, src), __shfl_sync(kAll, v.lo, src));
+}
+__device__ __forceinline__ df64 hd_shfl_up(df64 v, int d) {
+  return df64(__shfl_up_sync(kAll, v.hi, d), __shfl_up_sync(kAll, v.lo, d));
+}
+__device__ __forceinline__ df64 hd_shfl_down(df64 v, int d) {
+  return df64(__shfl_down_sync(kAll, v.hi, d), __shfl_down_sync(kAll, v.lo, d));
+}
+__device__ __forceinline__ df64 hd_warp_sum(df64 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add_fast(v, df64(__shfl_xor_sync(kAll, v.hi, o), __shfl_xor_sync(kAll, v.lo, o)));
+  return v;
+}
+// NaN-propagating maximum of magnitudes (float: the residual's size, not its value, is kept)
+__device__ __forceinline__ float hd_nan_max(float a, float b) { return (a < b || b != b) ? b : a; }
+__device__ __forceinline__ float hd_warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = hd_nan_max(v, __shfl_xor_sync(kAll, v, o));
+  return v;
+}
+
+// A double to double-float: the integer split for values in its range, the conversion
+// otherwise (values outside [2^-74, 2^57], infinities and NaN, which then propagate); the
+// warp takes the conversion branch only when one of its lanes needs it.
 template <int E>
-__global__ void __launch_bounds__(128) k_heat_forward(HeatArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= a.B) return;
+__device__ __forceinline__ void hd_load(const double (&x)[E], df64 (&v)[E]) {
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < E; ++q) ok &= df_split_trunc(x[q], v[q].hi, v[q].lo);
+  if (!__all_sync(kAll, ok)) {
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = df64(x[q]);
+  }
+}
+
+template <int E>
+struct HeatFactorDF {
+  df64 rho, comb, inv;   // comb = (rho / kappa) / (1 - rho^2)
+  df64 P[5];
+  df64 pl[E], pr[E], pf[E], pb[E];
+};
+
+template <int E>
+__device__ __forceinline__ void heat_factor_df(HeatFactorDF<E> &d, double alpha, double dx,
+                                               double dt, int nx, int lane) {
+  HeatFactor<E> f;
+  heat_factor<E>(f, alpha, dx, dt, nx, lane);
+  d.rho = df64(f.rho);
+  d.comb = df64(f.scale / (1.0 - f.rho * f.rho));
+  d.inv = df64(f.inv);
+#pragma unroll
+  for (int j = 0; j < 5; ++j) d.P[j] = df64(f.P[j]);
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    d.pl[q] = df64(f.pl[q]);
+    d.pr[q] = df64(f.pr[q]);
+    d.pf[q] = df64(f.pf[q]);
+    d.pb[q] = df64(f.pb[q]);
+  }
+}
+
+// y <- A^-1 y in double-float (values beyond nx are 0 on entry and on exit).  The two
+// first-order factors commute, (I - rho S)(I - rho S^-1) has the partial fractions
+//   ((I - rho S)^-1 + (I - rho S^-1)^-1 - I) / (1 - rho^2),
+// so the forward and the backward periodic recurrence both run on y, independently (two
+// interleaved chains instead of one after the other), and
+//   A^-1 y = (rho / kappa) / (1 - rho^2) (F + G - y).
+// rho solves kappa rho^2 - (1 + 2 kappa) rho + kappa = 0, i.e. kappa (1 - rho)^2 = rho, so the
+// factor times the bound |F|, |G| <= |y|_inf / (1 - rho) is 1 / (1 + rho) <= 1: the rounding
+// of the combination stays within a few units of 2^-47 |y|_inf.
+template <int E>
+__device__ __forceinline__ void heat_solve_df(const HeatFactorDF<E> &f, df64 (&y)[E], int nx,
+                                              int lane) {
+  const df64 zero(0.0f, 0.0f);
+  df64 F[E], G[E];
+  // F: z_i = y_i + rho z_{i-1}; G: x_i = y_i + rho x_{i+1} (each periodic)
+  df64 rf = zero, rb = zero;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    rf = hd_fma(f.rho, rf, y[q]);
+    F[q] = rf;
+    rb = hd_fma(f.rho, rb, y[E - 1 - q]);
+    G[E - 1 - q] = rb;
+  }
+  df64 vf = F[E - 1], vb = G[0];
+#pragma unroll
+  for (int j = 0; j < 5; ++j) {
+    const int d = 1 << j;
+    const df64 tf = hd_shfl_up(vf, d);
+    const df64 tb = hd_shfl_down(vb, d);
+    if (lane >= d) vf = hd_fma(f.P[j], tf, vf);
+    if (lane + d < 32) vb = hd_fma(f.P[j], tb, vb);
+  }
+  df64 cf = hd_shfl_up(vf, 1), cb = hd_shfl_down(vb, 1);
+  if (lane == 0) cf = zero;
+  if (lane == 31) cb = zero;
+  const int L = (nx - 1) / E, Lq = (nx - 1) - L * E;
+  df64 zl = zero;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    F[q] = hd_fma(f.pl[q], cf, F[q]);
+    G[q] = hd_fma(f.pr[q], cb, G[q]);
+    if (q == Lq) zl = F[q];
+  }
+  // the periodic wrap terms: rho^(i+1) z_{n-1} / (1 - rho^n), rho^(n-i) x_0 / (1 - rho^n)
+  zl = hd_shfl(zl, L) * f.inv;
+  const df64 x0 = hd_shfl(G[0], 0) * f.inv;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const df64 t = df_add_fast(hd_fma(f.pf[q], zl, F[q]), hd_fma(f.pb[q], x0, G[q]));
+    y[q] = (lane * E + q < nx) ? f.comb * df_sub_fast(t, y[q]) : zero;
+  }
+}
+
+// Periodic neighbours in double-float.
+template <int E>
+__device__ __forceinline__ void heat_neighbours_df(const df64 (&v)[E], df64 (&lft)[E],
+                                                   df64 (&rgt)[E], int nx, int lane) {
+  const int L = (nx - 1) / E, Lq = (nx - 1) - L * E;
+  df64 last(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < E; ++q)
+    if (q == Lq) last = v[q];
+  last = hd_shfl(last, L);
+  const df64 first = hd_shfl(v[0], 0);
+  const df64 up = hd_shfl_up(v[E - 1], 1);
+  const df64 dn = hd_shfl_down(v[0], 1);
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = lane * E + q;
+    lft[q] = (q > 0) ? v[q - 1] : ((lane > 0) ? up : last);
+    rgt[q] = (i == nx - 1) ? first : ((q < E - 1) ? v[q + 1] : dn);
+  }
+}
+
+// Per-sample constants of the residual rows in double-float.
+struct HeatRowsDF {
+  df64 c1, c2, c3;     // (1 + 2 kappa) / dt, (1 - 2 kappa) / dt, kappa / dt
+  df64 dx, half_dx, idt, ce;   // dx, dx / 2, 1 / dt, alpha / (4 dx)
+};
+
+__device__ __forceinline__ HeatRowsDF heat_rows_df(double alpha, double dx, double dt) {
+  const double kap = alpha * dt / (2.0 * dx * dx);
+  HeatRowsDF r;
+  r.c1 = df64((1.0 + 2.0 * kap) / dt);
+  r.c2 = df64((1.0 - 2.0 * kap) / dt);
+  r.c3 = df64(kap / dt);
+  r.dx = df64(dx);
+  r.half_dx = df64(0.5 * dx);
+  r.idt = df64(1.0 / dt);
+  r.ce = df64(alpha / (4.0 * dx));
+  return r;
+}
+
+// The mass, PDE and energy rows of slice k >= 1 in double-float (heat_slice_residual):
+// returns max |h| over the slice's rows, as a float magnitude (all lanes).
+template <int E>
+__device__ __forceinline__ float heat_slice_residual_df(const HeatRowsDF &c, const df64 &sum_g,
+                                                        const df64 (&cur)[E],
+                                                        const df64 (&prev)[E], df64 &e_prev,
+                                                        int nx, int lane) {
+  df64 s[E], sl[E], sr[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) s[q] = df_add_fast(cur[q], prev[q]);
+  heat_neighbours_df<E>(s, sl, sr, nx, lane);
+  float mx = 0.0f;
+  df64 su(0.0f, 0.0f), su2(0.0f, 0.0f), sd2(0.0f, 0.0f);
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    if (lane * E + q < nx) {
+      // ((1 + 2k) u^k - (1 - 2k) u^{k-1} - k (s_{i-1} + s_{i+1})) / dt
+      const df64 t = hd_fma(-c.c2, prev[q], c.c1 * cur[q]);
+      const df64 r = hd_fma(-c.c3, df_add_fast(sl[q], sr[q]), t);
+      mx = hd_nan_max(mx, fabsf(r.hi));
+      su = df_add_fast(su, cur[q]);
+      su2 = hd_fma(cur[q], cur[q], su2);
+      const df64 d = df_sub_fast(sr[q], s[q]);     // 2 dx D+ ubar
+      sd2 = hd_fma(d, d, sd2);
+    }
+  }
+  su = hd_warp_sum(su);
+  su2 = hd_warp_sum(su2);
+  sd2 = hd_warp_sum(sd2);
+  const df64 hm = c.dx * df_sub_fast(su, sum_g);
+  const df64 ek = c.half_dx * su2;
+  const df64 he = hd_fma(df_sub_fast(ek, e_prev), c.idt, c.ce * sd2);
+  e_prev = ek;
+  return hd_nan_max(hd_warp_max(mx), hd_nan_max(fabsf(hm.hi), fabsf(he.hi)));
+}
+
+// Forward projection of sample b in double-float.  Returns false, having written nothing that
+// the FP64 path does not overwrite, when a value leaves the double-float range: an IC value or
+// alpha up front (bad alpha included), a residual u_hat - u in the multiplier pass.
+template <int E>
+__device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int lane) {
+  const int nx = a.nx, nt = a.nt;
+  const double *pg = a.params + (size_t)b * (nx + 1);
+  const double alpha = pg[nx];
+  // alpha = 0 takes the FP64 path: there u^k = g exactly, which a 48-bit significand does not
+  // reproduce for every double g
+  if (!(alpha > 0.0) || !(alpha <= 1e30)) return false;
+  [[maybe_unused]] const long long nvar = (long long)a.B * nx * nt;
+  double g[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = lane * E + q;
+    g[q] = (i < nx && snap_in_bounds(SNAP_SITE_HEAT_G, (long long)b * (nx + 1) + i,
+                                     (long long)a.B * (nx + 1))) ? pg[i] : 0.0;
+  }
+  const df64 zero(0.0f, 0.0f);
+  df64 cur[E], prev[E];
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < E; ++q)
+    ok &= df_split_trunc(g[q], cur[q].hi, cur[q].lo) && fabs(g[q]) <= 0x1p60;
+  if (!__all_sync(kAll, ok)) return false;
+  double *ub = a.u_out + (size_t)b * nx * nt;
+  const double *uhb = a.uh + (size_t)b * nx * nt;
+  double *lb = a.lam + (size_t)b * a.n_rows;
+  HeatFactorDF<E> f;
+  heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
+  const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
+  df64 sg = zero, sq = zero;
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = lane * E + q;
+    if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + i, nvar)) ub[i] = g[q];
+    sg = df_add_fast(sg, cur[q]);
+    sq = hd_fma(cur[q], cur[q], sq);
+  }
+  const df64 sum_g = hd_warp_sum(sg);
+  df64 e_prev = c.half_dx * hd_warp_sum(sq);
+  float hmax = 0.0f;                  // IC rows and the mass row of slice 0 hold exactly
+  // u^k = 2 A^-1 u^{k-1} - u^{k-1}.  The residual rows of slice k - 1 are formed in the same
+  // iteration as the solve for slice k (independent chains the compiler interleaves).
+  auto advance = [&](int k, df64 (&z)[E]) {
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      z[q] = (i < nx) ? df_add_fast(df_scale2(z[q], 2.0f), -cur[q]) : zero;
+      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + (long long)k * nx + i, nvar))
+        ub[(size_t)k * nx + i] = df_to_double(z[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      prev[q] = cur[q];
+      cur[q] = z[q];
+    }
+  };
+  if (nt >= 2) {
+    df64 z[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) z[q] = cur[q];
+    heat_solve_df<E>(f, z, nx, lane);
+    advance(1, z);
+    for (int k = 2; k < nt; ++k) {
+#pragma unroll
+      for (int q = 0; q < E; ++q) z[q] = cur[q];
+      heat_solve_df<E>(f, z, nx, lane);
+      hmax = hd_nan_max(hmax, heat_slice_residual_df<E>(c, sum_g, cur, prev, e_prev, nx, lane));
+      advance(k, z);
+    }
+    hmax = hd_nan_max(hmax, heat_slice_residual_df<E>(c, sum_g, cur, prev, e_prev, nx, lane));
+  }
+  // backward substitution for the multipliers (u read back: written above by this warp)
+  __syncwarp();
+  const df64 dt_d = df64(a.dt);
+  df64 lam1[E], obj = zero;
+#pragma unroll
+  for (int q = 0; q < E; ++q) lam1[q] = zero;
+  bool in_range = true;
+  // the next step's u_hat and u are loaded one iteration ahead
+  double xh[E], xu[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = lane * E + q;
+    xh[q] = (i < nx) ? uhb[(size_t)(nt - 1) * nx + i] : 0.0;
+    xu[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;
+  }
+  for (int k = nt - 1; k >= 1; --k) {
+    double rd[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      rd[q] = xh[q] - xu[q];
+      xh[q] = (i < nx) ? uhb[(size_t)(k - 1) * nx + i] : 0.0;
+      xu[q] = (i < nx) ? ub[(size_t)(k - 1) * nx + i] : 0.0;
+    }
+    df64 y[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) in_range &= df_split_trunc(rd[q], y[q].hi, y[q].lo);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      obj = hd_fma(y[q], y[q], obj);
+      y[q] = (lane * E + q < nx) ? hd_fma(dt_d, y[q], df_scale2(lam1[q], 2.0f)) : zero;
+    }
+    heat_solve_df<E>(f, y, nx, lane);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      const df64 lk = (i < nx) ? df_sub_fast(y[q], lam1[q]) : zero;
+      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + (long long)(k - 1) * nx + i, a.n_rows))
+        lb[a.off_pde + (size_t)(k - 1) * nx + i] = df_to_double(lk);
+      lam1[q] = lk;
+    }
+  }
+  // a residual outside the split range (non-finite, huge or below 2^-74): the FP64 path
+  if (!__all_sync(kAll, in_range)) return false;
+  // IC multipliers: r^0 + (2 lambda^1 - A lambda^1) / dt = r^0 + c2 lambda^1 + c3 (l + r)
+  {
+    df64 ll[E], lr[E];
+    heat_neighbours_df<E>(lam1, ll, lr, nx, lane);
+    double r0[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) r0[q] = xh[q] - xu[q];   // slice 0, loaded by the last step
+    df64 v0[E];
+    bool ok0 = true;
+#pragma unroll
+    for (int q = 0; q < E; ++q) ok0 &= df_split_trunc(r0[q], v0[q].hi, v0[q].lo);
+    if (!__all_sync(kAll, ok0)) return false;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      if (i < nx) {
+        obj = hd_fma(v0[q], v0[q], obj);
+        lb[i] = df_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, lam1[q], v0[q])));
+      }
+    }
+  }
+  for (int k = lane; k < nt; k += 32) lb[a.off_mass + k] = 0.0;
+  for (int k = lane; k < nt - 1; k += 32) lb[a.off_energy + k] = 0.0;
+  const double objd = 0.5 * df_to_double(hd_warp_sum(obj));
+  const double hmaxd = df_f2d(hmax);
+  if (a.stats && lane == 0) {
+    snap_stats st;
+    st.iters = 1;
+    st.backtracks = 0;
+    st.corrections = 0;
+    st.h_inf = hmaxd;
+    st.kkt_inf = hmaxd;   // active rows (IC exact, PDE rows) at the returned u
+    st.obj = objd;
+    if (!(hmaxd == hmaxd) || isinf(hmaxd) || !(objd == objd) || isinf(objd)) st.status = SNAP_SAMPLE_NONFINITE;
+    else if (!(hmaxd <= a.tol_h)) st.status = SNAP_SAMPLE_RESIDUAL;
+    else st.status = SNAP_SAMPLE_OK;
+    a.stats[b] = st;
+  }
+  return true;
+}
+
+// Adjoint of sample b in double-float (heat_backward_fp64's recurrences).  Returns false,
+// having written only values that the FP64 path overwrites, when a value leaves the
+// double-float range (bad samples and alpha included).
+template <int E>
+__device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int lane) {
+  const int nx = a.nx, nt = a.nt;
+  const double *pg = a.params + (size_t)b * (nx + 1);
+  const double alpha = pg[nx];
+  if ((a.fwd_stats && a.fwd_stats[b].status != SNAP_SAMPLE_OK) || !(alpha >= 0.0) ||
+      !(alpha <= 1e30))
+    return false;
+  const double *gb = a.uh + (size_t)b * nx * nt;       // dL/du
+  const double *ub = a.u + (size_t)b * nx * nt;
+  double *gh = a.grad_uh + (size_t)b * nx * nt;
+  double *gp = a.grad_params ? a.grad_params + (size_t)b * (nx + 1) : nullptr;
+  const df64 zero(0.0f, 0.0f);
+  HeatFactorDF<E> f;
+  heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
+  const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
+  const df64 dt_d = df64(a.dt);
+  const df64 cd2 = df64(0.5 / (a.dx * a.dx));
+  bool ok = true;
+  df64 b1[E], nxt[E], dalpha = zero;
+  {
+    double x[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      b1[q] = zero;
+      x[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;   // u^k of the step below
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) ok &= df_split_trunc(x[q], nxt[q].hi, nxt[q].lo);
+  }
+  // gbar^k and u^{k-1} of the next step are loaded one iteration ahead
+  double xg[E], xu[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) {
+    const int i = lane * E + q;
+    xg[q] = (i < nx && nt > 1) ? gb[(size_t)(nt - 1) * nx + i] : 0.0;
+    xu[q] = (i < nx && nt > 1) ? ub[(size_t)(nt - 2) * nx + i] : 0.0;
+  }
+  for (int k = nt - 1; k >= 1; --k) {
+    df64 y[E], cur[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      ok &= df_split_trunc(xg[q], y[q].hi, y[q].lo);
+      ok &= df_split_trunc(xu[q], cur[q].hi, cur[q].lo);
+      xg[q] = (i < nx && k > 1) ? gb[(size_t)(k - 1) * nx + i] : 0.0;
+      xu[q] = (i < nx && k > 1) ? ub[(size_t)(k - 2) * nx + i] : 0.0;   // u^{k-2}
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+      y[q] = (lane * E + q < nx) ? hd_fma(dt_d, y[q], df_scale2(b1[q], 2.0f)) : zero;
+    heat_solve_df<E>(f, y, nx, lane);
+    // b^k . 1/2 D2 (u^k + u^{k-1})
+    df64 s[E], sl[E], sr[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      b1[q] = (lane * E + q < nx) ? df_sub_fast(y[q], b1[q]) : zero;
+      s[q] = df_add_fast(nxt[q], cur[q]);
+    }
+    heat_neighbours_df<E>(s, sl, sr, nx, lane);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      if (lane * E + q < nx) {
+        const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(s[q], 2.0f));
+        dalpha = hd_fma(b1[q], cd2 * d2, dalpha);
+      }
+      nxt[q] = cur[q];
+    }
+  }
+  if (!__all_sync(kAll, ok)) return false;
+  dalpha = hd_warp_sum(dalpha);
+  double g0[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) g0[q] = (lane * E + q < nx) ? gb[lane * E + q] : 0.0;
+  df64 v0[E];
+  bool ok0 = true;
+#pragma unroll
+  for (int q = 0; q < E; ++q) ok0 &= df_split_trunc(g0[q], v0[q].hi, v0[q].lo);
+  if (!__all_sync(kAll, ok0)) return false;
+  for (size_t i = lane; i < (size_t)nx * nt; i += 32) gh[i] = 0.0;
+  if (gp) {
+    df64 ll[E], lr[E];
+    heat_neighbours_df<E>(b1, ll, lr, nx, lane);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      // gbar^0 + (2 b^1 - A b^1) / dt = gbar^0 + c2 b^1 + c3 (l + r)
+      if (i < nx)
+        gp[i] = df_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, b1[q], v0[q])));
+    }
+    if (lane == 0) gp[nx] = df_to_double(dalpha);
+  }
+  return true;
+}
+
+// Forward projection of sample b in FP64: u (time chain), lambda (backward substitution),
+// statistics.  The path of a sample whose values leave the double-float range.
+template <int E>
+__device__ __noinline__ void heat_forward_fp64(const HeatArgs &a, int b, int lane) {
   const int nx = a.nx, nt = a.nt;
   const double *pg = a.params + (size_t)b * (nx + 1);
   const double alpha = pg[nx];
@@ -373,13 +842,11 @@ __global__ void __launch_bounds__(128) k_heat_residual(HeatArgs a) {
   if (a.h_inf && lane == 0) a.h_inf[b] = hmax;
 }
 
-// Adjoint: J^T b = gbar by the same backward substitution; dL/du_hat = 0,
-// dL/dg = b_IC, dL/dalpha = sum_k b^k . 1/2 D2 (u^k + u^{k-1}).
+// Adjoint of sample b in FP64: J^T b = gbar by the same backward substitution;
+// dL/du_hat = 0, dL/dg = b_IC, dL/dalpha = sum_k b^k . 1/2 D2 (u^k + u^{k-1}).  The path of a
+// sample whose values leave the double-float range.
 template <int E>
-__global__ void __launch_bounds__(128) k_heat_backward(HeatArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= a.B) return;
+__device__ __noinline__ void heat_backward_fp64(const HeatArgs &a, int b, int lane) {
   const int nx = a.nx, nt = a.nt;
   const double *pg = a.params + (size_t)b * (nx + 1);
   const double alpha = pg[nx];
@@ -446,12 +913,37 @@ __global__ void __launch_bounds__(128) k_heat_backward(HeatArgs a) {
   }
 }
 
+// One warp per sample, one sample per block (the samples spread over every SM): the
+// double-float chain, or the FP64 chain for a sample whose values leave its range (and for
+// E > 8, where the double-float arrays would spill).
+template <int E>
+__global__ void __launch_bounds__(32) k_heat_forward(HeatArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x;
+  if (b >= a.B) return;
+  if constexpr (E <= 8) {
+    if (heat_forward_df<E>(a, b, lane)) return;
+  }
+  heat_forward_fp64<E>(a, b, lane);
+}
+
+template <int E>
+__global__ void __launch_bounds__(32) k_heat_backward(HeatArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x;
+  if (b >= a.B) return;
+  if constexpr (E <= 8) {
+    if (heat_backward_df<E>(a, b, lane)) return;
+  }
+  heat_backward_fp64<E>(a, b, lane);
+}
+
 template <int E>
 void heat_launch(int kind, const HeatArgs &a, cudaStream_t s) {
   const unsigned blocks = (unsigned)(((long long)a.B * 32 + 127) / 128);
-  if (kind == 0) k_heat_forward<E><<<blocks, 128, 0, s>>>(a);
+  if (kind == 0) k_heat_forward<E><<<(unsigned)a.B, 32, 0, s>>>(a);
   else if (kind == 1) k_heat_residual<E><<<blocks, 128, 0, s>>>(a);
-  else k_heat_backward<E><<<blocks, 128, 0, s>>>(a);
+  else k_heat_backward<E><<<(unsigned)a.B, 32, 0, s>>>(a);
 }
 
 cudaError_t heat_dispatch(int kind, const HeatArgs &a, cudaStream_t s) {
