@@ -278,10 +278,14 @@ __device__ __forceinline__ void hd_load(const double (&x)[E], df64 (&v)[E]) {
   }
 }
 
+// The factor constants in double-float, with the lane masks folded into the multipliers so that
+// the solve has no lane-dependent branch: Pf[j] / Pb[j] are the scan multipliers of level j,
+// 0 on the lanes that take no contribution at that level (lane < 2^j, lane + 2^j > 31), and
+// pl / pr are 0 on lane 0 / lane 31 (no block before / after).
 template <int E>
 struct HeatFactorDF {
   df64 rho, comb, inv;   // comb = (rho / kappa) / (1 - rho^2)
-  df64 P[5];
+  df64 Pf[5], Pb[5];
   df64 pl[E], pr[E], pf[E], pb[E];
 };
 
@@ -293,12 +297,16 @@ __device__ __forceinline__ void heat_factor_df(HeatFactorDF<E> &d, double alpha,
   d.rho = df64(f.rho);
   d.comb = df64(f.scale / (1.0 - f.rho * f.rho));
   d.inv = df64(f.inv);
+  const df64 zero(0.0f, 0.0f);
 #pragma unroll
-  for (int j = 0; j < 5; ++j) d.P[j] = df64(f.P[j]);
+  for (int j = 0; j < 5; ++j) {
+    d.Pf[j] = (lane >= (1 << j)) ? df64(f.P[j]) : zero;
+    d.Pb[j] = (lane + (1 << j) < 32) ? df64(f.P[j]) : zero;
+  }
 #pragma unroll
   for (int q = 0; q < E; ++q) {
-    d.pl[q] = df64(f.pl[q]);
-    d.pr[q] = df64(f.pr[q]);
+    d.pl[q] = (lane > 0) ? df64(f.pl[q]) : zero;
+    d.pr[q] = (lane < 31) ? df64(f.pr[q]) : zero;
     d.pf[q] = df64(f.pf[q]);
     d.pb[q] = df64(f.pb[q]);
   }
@@ -327,18 +335,18 @@ __device__ __forceinline__ void heat_solve_df(const HeatFactorDF<E> &f, df64 (&y
     rb = hd_fma(f.rho, rb, y[E - 1 - q]);
     G[E - 1 - q] = rb;
   }
+  // block-end scans; a lane that takes no contribution has a zero multiplier (the shuffled
+  // value there is its own, finite), so every lane runs the same instructions
   df64 vf = F[E - 1], vb = G[0];
 #pragma unroll
   for (int j = 0; j < 5; ++j) {
     const int d = 1 << j;
     const df64 tf = hd_shfl_up(vf, d);
     const df64 tb = hd_shfl_down(vb, d);
-    if (lane >= d) vf = hd_fma(f.P[j], tf, vf);
-    if (lane + d < 32) vb = hd_fma(f.P[j], tb, vb);
+    vf = hd_fma(f.Pf[j], tf, vf);
+    vb = hd_fma(f.Pb[j], tb, vb);
   }
-  df64 cf = hd_shfl_up(vf, 1), cb = hd_shfl_down(vb, 1);
-  if (lane == 0) cf = zero;
-  if (lane == 31) cb = zero;
+  const df64 cf = hd_shfl_up(vf, 1), cb = hd_shfl_down(vb, 1);   // times pl = 0 / pr = 0 at the ends
   const int L = (nx - 1) / E, Lq = (nx - 1) - L * E;
   df64 zl = zero;
 #pragma unroll
@@ -353,11 +361,12 @@ __device__ __forceinline__ void heat_solve_df(const HeatFactorDF<E> &f, df64 (&y
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const df64 t = df_add_fast(hd_fma(f.pf[q], zl, F[q]), hd_fma(f.pb[q], x0, G[q]));
-    y[q] = (lane * E + q < nx) ? f.comb * df_sub_fast(t, y[q]) : zero;
+    const df64 v = f.comb * df_sub_fast(t, y[q]);
+    y[q] = (lane * E + q < nx) ? v : zero;
   }
 }
 
-// Periodic neighbours in double-float.
+// Periodic neighbours in double-float (0 beyond nx).
 template <int E>
 __device__ __forceinline__ void heat_neighbours_df(const df64 (&v)[E], df64 (&lft)[E],
                                                    df64 (&rgt)[E], int nx, int lane) {
@@ -370,11 +379,14 @@ __device__ __forceinline__ void heat_neighbours_df(const df64 (&v)[E], df64 (&lf
   const df64 first = hd_shfl(v[0], 0);
   const df64 up = hd_shfl_up(v[E - 1], 1);
   const df64 dn = hd_shfl_down(v[0], 1);
+  const df64 zero(0.0f, 0.0f);
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const int i = lane * E + q;
-    lft[q] = (q > 0) ? v[q - 1] : ((lane > 0) ? up : last);
-    rgt[q] = (i == nx - 1) ? first : ((q < E - 1) ? v[q + 1] : dn);
+    const df64 l = (q > 0) ? v[q - 1] : ((lane > 0) ? up : last);
+    const df64 r = (i == nx - 1) ? first : ((q < E - 1) ? v[q + 1] : dn);
+    lft[q] = (i < nx) ? l : zero;     // 0 beyond nx: no per-element guard in the callers
+    rgt[q] = (i < nx) ? r : zero;
   }
 }
 
@@ -397,47 +409,86 @@ __device__ __forceinline__ HeatRowsDF heat_rows_df(double alpha, double dx, doub
   return r;
 }
 
-// The mass, PDE and energy rows of slice k >= 1 in double-float (heat_slice_residual):
-// returns max |h| over the slice's rows, as a float magnitude (all lanes).
+// The rows of slice k >= 1 in double-float (heat_slice_residual), lane part: the PDE rows of
+// the lane's elements into the lane's running max |h| (mx), and the lane's partial sums of the
+// mass and energy rows, sum u^k, sum (u^k)^2 and sum (2 dx D+ ubar)^2.  The warp sums of the
+// partials are deferred to heat_rows_flush.
 template <int E>
-__device__ __forceinline__ float heat_slice_residual_df(const HeatRowsDF &c, const df64 &sum_g,
-                                                        const df64 (&cur)[E],
-                                                        const df64 (&prev)[E], df64 &e_prev,
-                                                        int nx, int lane) {
+__device__ __forceinline__ void heat_slice_rows_df(const HeatRowsDF &c, const df64 (&cur)[E],
+                                                   const df64 (&prev)[E], int nx, int lane,
+                                                   float &mx, df64 &su, df64 &su2, df64 &sd2) {
   df64 s[E], sl[E], sr[E];
 #pragma unroll
   for (int q = 0; q < E; ++q) s[q] = df_add_fast(cur[q], prev[q]);
   heat_neighbours_df<E>(s, sl, sr, nx, lane);
-  float mx = 0.0f;
-  df64 su(0.0f, 0.0f), su2(0.0f, 0.0f), sd2(0.0f, 0.0f);
+  su = su2 = sd2 = df64(0.0f, 0.0f);
+  // every term is 0 beyond nx (u and the neighbours are), so no element guard
 #pragma unroll
   for (int q = 0; q < E; ++q) {
-    if (lane * E + q < nx) {
-      // ((1 + 2k) u^k - (1 - 2k) u^{k-1} - k (s_{i-1} + s_{i+1})) / dt
-      const df64 t = hd_fma(-c.c2, prev[q], c.c1 * cur[q]);
-      const df64 r = hd_fma(-c.c3, df_add_fast(sl[q], sr[q]), t);
-      mx = hd_nan_max(mx, fabsf(r.hi));
-      su = df_add_fast(su, cur[q]);
-      su2 = hd_fma(cur[q], cur[q], su2);
-      const df64 d = df_sub_fast(sr[q], s[q]);     // 2 dx D+ ubar
-      sd2 = hd_fma(d, d, sd2);
-    }
+    // ((1 + 2k) u^k - (1 - 2k) u^{k-1} - k (s_{i-1} + s_{i+1})) / dt
+    const df64 t = hd_fma(-c.c2, prev[q], c.c1 * cur[q]);
+    const df64 r = hd_fma(-c.c3, df_add_fast(sl[q], sr[q]), t);
+    mx = hd_nan_max(mx, fabsf(r.hi));
+    su = df_add_fast(su, cur[q]);
+    su2 = hd_fma(cur[q], cur[q], su2);
+    const df64 d = df_sub_fast(sr[q], s[q]);     // 2 dx D+ ubar
+    sd2 = hd_fma(d, d, sd2);
   }
-  su = hd_warp_sum(su);
-  su2 = hd_warp_sum(su2);
-  sd2 = hd_warp_sum(sd2);
-  const df64 hm = c.dx * df_sub_fast(su, sum_g);
-  const df64 ek = c.half_dx * su2;
-  const df64 he = hd_fma(df_sub_fast(ek, e_prev), c.idt, c.ce * sd2);
-  e_prev = ek;
-  return hd_nan_max(hd_warp_max(mx), hd_nan_max(fabsf(hm.hi), fabsf(he.hi)));
 }
 
-// Forward projection of sample b in double-float.  Returns false, having written nothing that
-// the FP64 path does not overwrite, when a value leaves the double-float range: an IC value or
-// alpha up front (bad alpha included), a residual u_hat - u in the multiplier pass.
+// Per-lane partial sums of up to 32 consecutive slices, one row per slice, padded to 33
+// columns so that the transposed reads of heat_rows_flush fall in distinct banks.
+struct HeatRowSums {
+  df64 su[32][33], su2[32][33], sd2[32][33];
+};
+
+// The mass and energy rows of the n (<= 32) slices whose partials fill rows 0 .. n-1: lane j
+// sums row j over the 32 lanes; the energy row of slice j takes E_{j-1} from lane j - 1 (lane
+// 0 from e_last, the last energy of the previous group).
+__device__ __forceinline__ void heat_rows_flush(const HeatRowsDF &c, const df64 &sum_g,
+                                                HeatRowSums &rs, int n, df64 &e_last, float &mx,
+                                                int lane) {
+  __syncwarp();
+  df64 su(0.0f, 0.0f), su2(0.0f, 0.0f), sd2(0.0f, 0.0f);
+  const int j = lane < n ? lane : n - 1;
+#pragma unroll 8
+  for (int l = 0; l < 32; ++l) {
+    su = df_add_fast(su, rs.su[j][l]);
+    su2 = df_add_fast(su2, rs.su2[j][l]);
+    sd2 = df_add_fast(sd2, rs.sd2[j][l]);
+  }
+  __syncwarp();
+  const df64 hm = c.dx * df_sub_fast(su, sum_g);
+  const df64 ek = c.half_dx * su2;
+  df64 ep = hd_shfl_up(ek, 1);
+  if (lane == 0) ep = e_last;
+  const df64 he = hd_fma(df_sub_fast(ek, ep), c.idt, c.ce * sd2);
+  if (lane < n) mx = hd_nan_max(mx, hd_nan_max(fabsf(hm.hi), fabsf(he.hi)));
+  e_last = hd_shfl(ek, n - 1);
+}
+
+// df64 -> double by two conversions and one FP64 addition: three issue slots against about
+// 25 integer operations for df_to_double; the FP64 pipe is otherwise idle in these chains.
+__device__ __forceinline__ double hd_to_double(df64 x) { return (double)x.hi + (double)x.lo; }
+
+// Statistics the two warps of a forward block exchange at the second barrier.
+struct HeatXchg {
+  double obj;
+  float hmax;
+  int ok0, ok1;
+};
+
+// Forward projection of sample b in double-float, by the two warps of the block.  Warp 0 runs
+// the time chains: u^k = 2 A^-1 u^{k-1} - u^{k-1}, then the multipliers by backward
+// substitution.  Once u is written, warp 1 evaluates the rows of every slice from the written
+// u (the residual statistics) and the objective, while warp 0 runs the multiplier chain.  Both
+// warps pass the two block barriers exactly once on every path through the function, and
+// return the same value: false, having written nothing that the FP64 path does not overwrite,
+// when a value leaves the double-float range (alpha = 0 or bad alpha, an IC value up front; a
+// residual u_hat - u or a written u value afterwards).
 template <int E>
-__device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int lane) {
+__device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int lane, int w,
+                                                HeatRowSums &rs, HeatXchg &xc) {
   const int nx = a.nx, nt = a.nt;
   const double *pg = a.params + (size_t)b * (nx + 1);
   const double alpha = pg[nx];
@@ -453,130 +504,156 @@ __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int la
                                      (long long)a.B * (nx + 1))) ? pg[i] : 0.0;
   }
   const df64 zero(0.0f, 0.0f);
-  df64 cur[E], prev[E];
+  df64 cur[E];
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < E; ++q)
     ok &= df_split_trunc(g[q], cur[q].hi, cur[q].lo) && fabs(g[q]) <= 0x1p60;
-  if (!__all_sync(kAll, ok)) return false;
+  if (!__all_sync(kAll, ok)) return false;    // the same data, so the same decision, in both warps
   double *ub = a.u_out + (size_t)b * nx * nt;
   const double *uhb = a.uh + (size_t)b * nx * nt;
   double *lb = a.lam + (size_t)b * a.n_rows;
-  HeatFactorDF<E> f;
-  heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
   const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
-  df64 sg = zero, sq = zero;
-#pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const int i = lane * E + q;
-    if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + i, nvar)) ub[i] = g[q];
-    sg = df_add_fast(sg, cur[q]);
-    sq = hd_fma(cur[q], cur[q], sq);
-  }
-  const df64 sum_g = hd_warp_sum(sg);
-  df64 e_prev = c.half_dx * hd_warp_sum(sq);
-  float hmax = 0.0f;                  // IC rows and the mass row of slice 0 hold exactly
-  // u^k = 2 A^-1 u^{k-1} - u^{k-1}.  The residual rows of slice k - 1 are formed in the same
-  // iteration as the solve for slice k (independent chains the compiler interleaves).
-  auto advance = [&](int k, df64 (&z)[E]) {
+  HeatFactorDF<E> f;
+  if (w == 0) {
+    heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      z[q] = (i < nx) ? df_add_fast(df_scale2(z[q], 2.0f), -cur[q]) : zero;
-      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + (long long)k * nx + i, nvar))
-        ub[(size_t)k * nx + i] = df_to_double(z[q]);
+      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + i, nvar)) ub[i] = g[q];
     }
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      prev[q] = cur[q];
-      cur[q] = z[q];
-    }
-  };
-  if (nt >= 2) {
-    df64 z[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) z[q] = cur[q];
-    heat_solve_df<E>(f, z, nx, lane);
-    advance(1, z);
-    for (int k = 2; k < nt; ++k) {
+    for (int k = 1; k < nt; ++k) {
+      df64 z[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) z[q] = cur[q];
       heat_solve_df<E>(f, z, nx, lane);
-      hmax = hd_nan_max(hmax, heat_slice_residual_df<E>(c, sum_g, cur, prev, e_prev, nx, lane));
-      advance(k, z);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int i = lane * E + q;
+        cur[q] = df_add_fast(df_scale2(z[q], 2.0f), -cur[q]);   // 0 beyond nx
+        if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + (long long)k * nx + i, nvar))
+          ub[(size_t)k * nx + i] = hd_to_double(cur[q]);
+      }
     }
-    hmax = hd_nan_max(hmax, heat_slice_residual_df<E>(c, sum_g, cur, prev, e_prev, nx, lane));
   }
-  // backward substitution for the multipliers (u read back: written above by this warp)
-  __syncwarp();
-  const df64 dt_d = df64(a.dt);
-  df64 lam1[E], obj = zero;
+  __syncthreads();                    // u written
+  if (w == 0) {
+    // multipliers by backward substitution; the next step's u_hat and u loaded one ahead
+    const df64 dt_d = df64(a.dt);
+    df64 lam1[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) lam1[q] = zero;
-  bool in_range = true;
-  // the next step's u_hat and u are loaded one iteration ahead
-  double xh[E], xu[E];
-#pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const int i = lane * E + q;
-    xh[q] = (i < nx) ? uhb[(size_t)(nt - 1) * nx + i] : 0.0;
-    xu[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;
-  }
-  for (int k = nt - 1; k >= 1; --k) {
-    double rd[E];
+    for (int q = 0; q < E; ++q) lam1[q] = zero;
+    bool in_range = true;
+    double xh[E], xu[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      rd[q] = xh[q] - xu[q];
-      xh[q] = (i < nx) ? uhb[(size_t)(k - 1) * nx + i] : 0.0;
-      xu[q] = (i < nx) ? ub[(size_t)(k - 1) * nx + i] : 0.0;
+      xh[q] = (i < nx) ? uhb[(size_t)(nt - 1) * nx + i] : 0.0;
+      xu[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;
     }
-    df64 y[E];
+    for (int k = nt - 1; k >= 1; --k) {
+      df64 y[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) in_range &= df_split_trunc(rd[q], y[q].hi, y[q].lo);
+      for (int q = 0; q < E; ++q) {
+        const int i = lane * E + q;
+        in_range &= df_split_trunc(xh[q] - xu[q], y[q].hi, y[q].lo);
+        xh[q] = (i < nx) ? uhb[(size_t)(k - 1) * nx + i] : 0.0;
+        xu[q] = (i < nx) ? ub[(size_t)(k - 1) * nx + i] : 0.0;
+      }
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-      obj = hd_fma(y[q], y[q], obj);
-      y[q] = (lane * E + q < nx) ? hd_fma(dt_d, y[q], df_scale2(lam1[q], 2.0f)) : zero;
+      for (int q = 0; q < E; ++q)
+        y[q] = hd_fma(dt_d, y[q], df_scale2(lam1[q], 2.0f));   // 0 beyond nx
+      heat_solve_df<E>(f, y, nx, lane);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int i = lane * E + q;
+        const df64 lk = df_sub_fast(y[q], lam1[q]);
+        if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + (long long)(k - 1) * nx + i, a.n_rows))
+          lb[a.off_pde + (size_t)(k - 1) * nx + i] = hd_to_double(lk);
+        lam1[q] = lk;
+      }
     }
-    heat_solve_df<E>(f, y, nx, lane);
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int i = lane * E + q;
-      const df64 lk = (i < nx) ? df_sub_fast(y[q], lam1[q]) : zero;
-      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + (long long)(k - 1) * nx + i, a.n_rows))
-        lb[a.off_pde + (size_t)(k - 1) * nx + i] = df_to_double(lk);
-      lam1[q] = lk;
-    }
-  }
-  // a residual outside the split range (non-finite, huge or below 2^-74): the FP64 path
-  if (!__all_sync(kAll, in_range)) return false;
-  // IC multipliers: r^0 + (2 lambda^1 - A lambda^1) / dt = r^0 + c2 lambda^1 + c3 (l + r)
-  {
-    df64 ll[E], lr[E];
+    // IC multipliers: r^0 + (2 lambda^1 - A lambda^1) / dt = r^0 + c2 lambda^1 + c3 (l + r),
+    // r^0 from the slice-0 values the last step loaded
+    df64 ll[E], lr[E], v0[E];
     heat_neighbours_df<E>(lam1, ll, lr, nx, lane);
-    double r0[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) r0[q] = xh[q] - xu[q];   // slice 0, loaded by the last step
-    df64 v0[E];
-    bool ok0 = true;
+    for (int q = 0; q < E; ++q) in_range &= df_split_trunc(xh[q] - xu[q], v0[q].hi, v0[q].lo);
 #pragma unroll
-    for (int q = 0; q < E; ++q) ok0 &= df_split_trunc(r0[q], v0[q].hi, v0[q].lo);
-    if (!__all_sync(kAll, ok0)) return false;
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      if (i < nx)
+        lb[i] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, lam1[q], v0[q])));
+    }
+    for (int k = lane; k < nt; k += 32) lb[a.off_mass + k] = 0.0;
+    for (int k = lane; k < nt - 1; k += 32) lb[a.off_energy + k] = 0.0;
+    in_range = __all_sync(kAll, in_range);
+    if (lane == 0) xc.ok0 = in_range;
+  } else {
+    // the rows of slices 1 .. nt-1 from the written u, and the objective 1/2 |u_hat - u|^2
+    df64 sg = zero, sq = zero;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      sg = df_add_fast(sg, cur[q]);
+      sq = hd_fma(cur[q], cur[q], sq);
+    }
+    const df64 sum_g = hd_warp_sum(sg);
+    df64 e_last = c.half_dx * hd_warp_sum(sq);   // energy of slice 0
+    float hmax = 0.0f;                  // IC rows and the mass row of slice 0 hold exactly
+    double obj = 0.0;
+    bool in_range = true;
+    double xh[E], xu[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
       if (i < nx) {
-        obj = hd_fma(v0[q], v0[q], obj);
-        lb[i] = df_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, lam1[q], v0[q])));
+        const double r0 = uhb[i] - g[q];
+        obj = fma(r0, r0, obj);
       }
+      xh[q] = (i < nx && nt > 1) ? uhb[(size_t)nx + i] : 0.0;
+      xu[q] = (i < nx && nt > 1) ? ub[(size_t)nx + i] : 0.0;
+    }
+    df64 prev[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) prev[q] = cur[q];
+    int nrow = 0;
+    for (int k = 1; k < nt; ++k) {
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int i = lane * E + q;
+        const double rd = xh[q] - xu[q];
+        obj = fma(rd, rd, obj);
+        in_range &= df_split_trunc(xu[q], cur[q].hi, cur[q].lo);
+        xh[q] = (i < nx && k + 1 < nt) ? uhb[(size_t)(k + 1) * nx + i] : 0.0;
+        xu[q] = (i < nx && k + 1 < nt) ? ub[(size_t)(k + 1) * nx + i] : 0.0;
+      }
+      df64 su, su2, sd2;
+      heat_slice_rows_df<E>(c, cur, prev, nx, lane, hmax, su, su2, sd2);
+      rs.su[nrow][lane] = su;
+      rs.su2[nrow][lane] = su2;
+      rs.sd2[nrow][lane] = sd2;
+      if (++nrow == 32) {
+        heat_rows_flush(c, sum_g, rs, 32, e_last, hmax, lane);
+        nrow = 0;
+      }
+#pragma unroll
+      for (int q = 0; q < E; ++q) prev[q] = cur[q];
+    }
+    if (nrow > 0) heat_rows_flush(c, sum_g, rs, nrow, e_last, hmax, lane);
+    hmax = hd_warp_max(hmax);
+    obj = h_warp_sum(obj);
+    in_range = __all_sync(kAll, in_range);
+    if (lane == 0) {
+      xc.hmax = hmax;
+      xc.obj = obj;
+      xc.ok1 = in_range;
     }
   }
-  for (int k = lane; k < nt; k += 32) lb[a.off_mass + k] = 0.0;
-  for (int k = lane; k < nt - 1; k += 32) lb[a.off_energy + k] = 0.0;
-  const double objd = 0.5 * df_to_double(hd_warp_sum(obj));
-  const double hmaxd = df_f2d(hmax);
-  if (a.stats && lane == 0) {
+  __syncthreads();                    // multipliers and statistics done
+  if (!(xc.ok0 && xc.ok1)) return false;
+  if (w == 0 && lane == 0 && a.stats) {
+    const double hmaxd = (double)xc.hmax;
+    const double objd = 0.5 * xc.obj;
     snap_stats st;
     st.iters = 1;
     st.backtracks = 0;
@@ -645,23 +722,21 @@ __device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int l
       xu[q] = (i < nx && k > 1) ? ub[(size_t)(k - 2) * nx + i] : 0.0;   // u^{k-2}
     }
 #pragma unroll
-    for (int q = 0; q < E; ++q)
-      y[q] = (lane * E + q < nx) ? hd_fma(dt_d, y[q], df_scale2(b1[q], 2.0f)) : zero;
+    for (int q = 0; q < E; ++q) y[q] = hd_fma(dt_d, y[q], df_scale2(b1[q], 2.0f));   // 0 beyond nx
     heat_solve_df<E>(f, y, nx, lane);
     // b^k . 1/2 D2 (u^k + u^{k-1})
     df64 s[E], sl[E], sr[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      b1[q] = (lane * E + q < nx) ? df_sub_fast(y[q], b1[q]) : zero;
+      b1[q] = df_sub_fast(y[q], b1[q]);   // 0 beyond nx
       s[q] = df_add_fast(nxt[q], cur[q]);
     }
     heat_neighbours_df<E>(s, sl, sr, nx, lane);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
-      if (lane * E + q < nx) {
-        const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(s[q], 2.0f));
-        dalpha = hd_fma(b1[q], cd2 * d2, dalpha);
-      }
+      // 0 beyond nx (b^k, s and the neighbours are)
+      const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(s[q], 2.0f));
+      dalpha = hd_fma(b1[q], cd2 * d2, dalpha);
       nxt[q] = cur[q];
     }
   }
@@ -684,9 +759,9 @@ __device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int l
       const int i = lane * E + q;
       // gbar^0 + (2 b^1 - A b^1) / dt = gbar^0 + c2 b^1 + c3 (l + r)
       if (i < nx)
-        gp[i] = df_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, b1[q], v0[q])));
+        gp[i] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, b1[q], v0[q])));
     }
-    if (lane == 0) gp[nx] = df_to_double(dalpha);
+    if (lane == 0) gp[nx] = hd_to_double(dalpha);
   }
   return true;
 }
@@ -913,18 +988,20 @@ __device__ __noinline__ void heat_backward_fp64(const HeatArgs &a, int b, int la
   }
 }
 
-// One warp per sample, one sample per block (the samples spread over every SM): the
-// double-float chain, or the FP64 chain for a sample whose values leave its range (and for
-// E > 8, where the double-float arrays would spill).
+// One sample per block (the samples spread over every SM): the double-float chains (two warps
+// in the forward, one in the adjoint), or the FP64 chain in warp 0 for a sample whose values
+// leave the double-float range (and for E > 8, where the double-float arrays would spill).
 template <int E>
-__global__ void __launch_bounds__(32) k_heat_forward(HeatArgs a) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(64) k_heat_forward(HeatArgs a) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x;
   if (b >= a.B) return;
   if constexpr (E <= 8) {
-    if (heat_forward_df<E>(a, b, lane)) return;
+    __shared__ HeatRowSums rs;
+    __shared__ HeatXchg xc;
+    if (heat_forward_df<E>(a, b, lane, w, rs, xc)) return;
   }
-  heat_forward_fp64<E>(a, b, lane);
+  if (w == 0) heat_forward_fp64<E>(a, b, lane);
 }
 
 template <int E>
@@ -941,7 +1018,7 @@ __global__ void __launch_bounds__(32) k_heat_backward(HeatArgs a) {
 template <int E>
 void heat_launch(int kind, const HeatArgs &a, cudaStream_t s) {
   const unsigned blocks = (unsigned)(((long long)a.B * 32 + 127) / 128);
-  if (kind == 0) k_heat_forward<E><<<(unsigned)a.B, 32, 0, s>>>(a);
+  if (kind == 0) k_heat_forward<E><<<(unsigned)a.B, 64, 0, s>>>(a);
   else if (kind == 1) k_heat_residual<E><<<blocks, 128, 0, s>>>(a);
   else k_heat_backward<E><<<(unsigned)a.B, 32, 0, s>>>(a);
 }
