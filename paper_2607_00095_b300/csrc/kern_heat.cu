@@ -241,6 +241,24 @@ __device__ __forceinline__ df64 hd_fma(df64 a, df64 b, df64 c) {
   return df_fast_two_sum(s.hi, s.lo + (e + c.lo));
 }
 
+// Two independent hd_fma, statement by statement interleaved (two latency chains in flight)
+__device__ __forceinline__ void hd_fma2(df64 a1, df64 b1, df64 c1, df64 a2, df64 b2, df64 c2,
+                                        df64 &r1, df64 &r2) {
+  const float p1 = a1.hi * b1.hi, p2 = a2.hi * b2.hi;
+  float e1 = fmaf(a1.hi, b1.hi, -p1), e2 = fmaf(a2.hi, b2.hi, -p2);
+  e1 = fmaf(a1.hi, b1.lo, e1);
+  e2 = fmaf(a2.hi, b2.lo, e2);
+  e1 = fmaf(a1.lo, b1.hi, e1);
+  e2 = fmaf(a2.lo, b2.hi, e2);
+  const float s1 = p1 + c1.hi, s2 = p2 + c2.hi;
+  const float q1 = s1 - p1, q2 = s2 - p2;
+  const float t1 = (p1 - (s1 - q1)) + (c1.hi - q1), t2 = (p2 - (s2 - q2)) + (c2.hi - q2);
+  const float l1 = t1 + (e1 + c1.lo), l2 = t2 + (e2 + c2.lo);
+  const float h1 = s1 + l1, h2 = s2 + l2;
+  r1 = df64(h1, l1 - (h1 - s1));
+  r2 = df64(h2, l2 - (h2 - s2));
+}
+
 __device__ __forceinline__ df64 hd_shfl(df64 v, int src) {
   return df64(__shfl_sync(kAll, v.hi, src), __shfl_sync(kAll, v.lo, src));
 }
@@ -256,6 +274,19 @@ __device__ __forceinline__ df64 hd_warp_sum(df64 v) {
     v = df_add_fast(v, df64(__shfl_xor_sync(kAll, v.hi, o), __shfl_xor_sync(kAll, v.lo, o)));
   return v;
 }
+// v[j] for a run-time j (warp-uniform) by selects: an indexed register array would go to local
+// memory, and an if per element would split the caller's straight-line code into blocks
+template <int E>
+__device__ __forceinline__ df64 hd_pick(const df64 (&v)[E], int j) {
+  df64 r = v[0];
+#pragma unroll
+  for (int q = 1; q < E; ++q) {
+    r.hi = (j == q) ? v[q].hi : r.hi;
+    r.lo = (j == q) ? v[q].lo : r.lo;
+  }
+  return r;
+}
+
 // NaN-propagating maximum of magnitudes (float: the residual's size, not its value, is kept)
 __device__ __forceinline__ float hd_nan_max(float a, float b) { return (a < b || b != b) ? b : a; }
 __device__ __forceinline__ float hd_warp_max(float v) {
@@ -330,9 +361,8 @@ __device__ __forceinline__ void heat_solve_df(const HeatFactorDF<E> &f, df64 (&y
   df64 rf = zero, rb = zero;
 #pragma unroll
   for (int q = 0; q < E; ++q) {
-    rf = hd_fma(f.rho, rf, y[q]);
+    hd_fma2(f.rho, rf, y[q], f.rho, rb, y[E - 1 - q], rf, rb);
     F[q] = rf;
-    rb = hd_fma(f.rho, rb, y[E - 1 - q]);
     G[E - 1 - q] = rb;
   }
   // block-end scans; a lane that takes no contribution has a zero multiplier (the shuffled
@@ -343,20 +373,14 @@ __device__ __forceinline__ void heat_solve_df(const HeatFactorDF<E> &f, df64 (&y
     const int d = 1 << j;
     const df64 tf = hd_shfl_up(vf, d);
     const df64 tb = hd_shfl_down(vb, d);
-    vf = hd_fma(f.Pf[j], tf, vf);
-    vb = hd_fma(f.Pb[j], tb, vb);
+    hd_fma2(f.Pf[j], tf, vf, f.Pb[j], tb, vb, vf, vb);
   }
   const df64 cf = hd_shfl_up(vf, 1), cb = hd_shfl_down(vb, 1);   // times pl = 0 / pr = 0 at the ends
   const int L = (nx - 1) / E, Lq = (nx - 1) - L * E;
-  df64 zl = zero;
 #pragma unroll
-  for (int q = 0; q < E; ++q) {
-    F[q] = hd_fma(f.pl[q], cf, F[q]);
-    G[q] = hd_fma(f.pr[q], cb, G[q]);
-    if (q == Lq) zl = F[q];
-  }
+  for (int q = 0; q < E; ++q) hd_fma2(f.pl[q], cf, F[q], f.pr[q], cb, G[q], F[q], G[q]);
   // the periodic wrap terms: rho^(i+1) z_{n-1} / (1 - rho^n), rho^(n-i) x_0 / (1 - rho^n)
-  zl = hd_shfl(zl, L) * f.inv;
+  const df64 zl = hd_shfl(hd_pick<E>(F, Lq), L) * f.inv;
   const df64 x0 = hd_shfl(G[0], 0) * f.inv;
 #pragma unroll
   for (int q = 0; q < E; ++q) {
@@ -371,11 +395,7 @@ template <int E>
 __device__ __forceinline__ void heat_neighbours_df(const df64 (&v)[E], df64 (&lft)[E],
                                                    df64 (&rgt)[E], int nx, int lane) {
   const int L = (nx - 1) / E, Lq = (nx - 1) - L * E;
-  df64 last(0.0f, 0.0f);
-#pragma unroll
-  for (int q = 0; q < E; ++q)
-    if (q == Lq) last = v[q];
-  last = hd_shfl(last, L);
+  const df64 last = hd_shfl(hd_pick<E>(v, Lq), L);
   const df64 first = hd_shfl(v[0], 0);
   const df64 up = hd_shfl_up(v[E - 1], 1);
   const df64 dn = hd_shfl_down(v[0], 1);
@@ -471,24 +491,35 @@ __device__ __forceinline__ void heat_rows_flush(const HeatRowsDF &c, const df64 
 // 25 integer operations for df_to_double; the FP64 pipe is otherwise idle in these chains.
 __device__ __forceinline__ double hd_to_double(df64 x) { return (double)x.hi + (double)x.lo; }
 
-// Statistics the two warps of a forward block exchange at the second barrier.
+// Statistics the two warps of a forward block exchange at the last barrier.
 struct HeatXchg {
   double obj;
   float hmax;
-  int ok0, ok1;
+  int ok;
+};
+
+// Double-buffered hand-over slots between the two warps of a block: one df64 per element of a
+// slice, [parity][q][lane] (consecutive lanes, consecutive words).
+template <int E>
+struct HeatSlots {
+  df64 u[2][E][32];   // forward chain: u^k, warp 0 -> warp 1
+  df64 r[2][E][32];   // multiplier chain: dt r^k (r^0 itself), warp 1 -> warp 0
+  df64 l[2][E][32];   // multiplier chain: lambda^k, warp 0 -> warp 1
 };
 
 // Forward projection of sample b in double-float, by the two warps of the block.  Warp 0 runs
-// the time chains: u^k = 2 A^-1 u^{k-1} - u^{k-1}, then the multipliers by backward
-// substitution.  Once u is written, warp 1 evaluates the rows of every slice from the written
-// u (the residual statistics) and the objective, while warp 0 runs the multiplier chain.  Both
-// warps pass the two block barriers exactly once on every path through the function, and
-// return the same value: false, having written nothing that the FP64 path does not overwrite,
-// when a value leaves the double-float range (alpha = 0 or bad alpha, an IC value up front; a
-// residual u_hat - u or a written u value afterwards).
+// only the time chains, u^k = 2 A^-1 u^{k-1} - u^{k-1} and then the multipliers by backward
+// substitution, handing each slice over through HeatSlots; warp 1 does everything off the
+// chains one step behind or ahead: it converts and stores u and lambda, evaluates the rows of
+// every slice (the residual statistics) and the objective, and prepares dt r^k = dt (u_hat - u)
+// for the multiplier chain.  One block barrier per step; both warps run the same loops, so
+// every barrier is reached by both on every path, and both return the same value: false,
+// having written nothing that the FP64 path does not overwrite, when a value leaves the
+// double-float range (alpha = 0 or bad alpha, an IC value up front; a residual u_hat - u).
 template <int E>
 __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int lane, int w,
-                                                HeatRowSums &rs, HeatXchg &xc) {
+                                                HeatRowSums &rs, HeatSlots<E> &sl,
+                                                HeatXchg &xc) {
   const int nx = a.nx, nt = a.nt;
   const double *pg = a.params + (size_t)b * (nx + 1);
   const double alpha = pg[nx];
@@ -514,131 +545,158 @@ __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int la
   const double *uhb = a.uh + (size_t)b * nx * nt;
   double *lb = a.lam + (size_t)b * a.n_rows;
   const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
+  const df64 dt_d = df64(a.dt);
   HeatFactorDF<E> f;
-  if (w == 0) {
-    heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
+  if (w == 0) heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
+  // warp 1: row statistics and objective
+  df64 sum_g = zero, e_last = zero, prev[E];
+  float hmax = 0.0f;                  // IC rows and the mass row of slice 0 hold exactly
+  double obj = 0.0;
+  bool in_range = true;
+  int nrow = 0;
+  double xh[E];                       // u_hat of the next slice to take, loaded one step ahead
+  if (w == 1) {
+    df64 sg = zero, sq = zero;
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + i, nvar)) ub[i] = g[q];
+      sg = df_add_fast(sg, cur[q]);
+      sq = hd_fma(cur[q], cur[q], sq);
+      prev[q] = cur[q];
+      if (i < nx) {
+        if (snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + i, nvar)) ub[i] = g[q];
+        const double r0 = uhb[i] - g[q];
+        obj = fma(r0, r0, obj);
+      }
+      xh[q] = (i < nx && nt > 1) ? uhb[(size_t)nx + i] : 0.0;
     }
-    for (int k = 1; k < nt; ++k) {
+    sum_g = hd_warp_sum(sg);
+    e_last = c.half_dx * hd_warp_sum(sq);   // energy of slice 0
+  }
+  // warp 1 takes slice k (1 <= k < nt) from its slot: stores u^k, adds its objective term (from
+  // the stored double) and its rows (with u^{k-1} = prev)
+  auto take = [&](int k) {
+    df64 v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = sl.u[k & 1][q][lane];
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      const double ud = hd_to_double(v[q]);
+      if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + (long long)k * nx + i, nvar))
+        ub[(size_t)k * nx + i] = ud;
+      const double rd = xh[q] - ud;                   // 0 beyond nx
+      obj = fma(rd, rd, obj);
+      xh[q] = (i < nx && k + 1 < nt) ? uhb[(size_t)(k + 1) * nx + i] : 0.0;
+    }
+    df64 su, su2, sd2;
+    heat_slice_rows_df<E>(c, v, prev, nx, lane, hmax, su, su2, sd2);
+    rs.su[nrow][lane] = su;
+    rs.su2[nrow][lane] = su2;
+    rs.sd2[nrow][lane] = sd2;
+    if (++nrow == 32) {
+      heat_rows_flush(c, sum_g, rs, 32, e_last, hmax, lane);
+      nrow = 0;
+    }
+#pragma unroll
+    for (int q = 0; q < E; ++q) prev[q] = v[q];
+  };
+  // the forward chain: iteration k computes u^k (warp 0) and takes slice k - 1 (warp 1)
+  for (int k = 1; k < nt; ++k) {
+    if (w == 0) {
       df64 z[E];
 #pragma unroll
       for (int q = 0; q < E; ++q) z[q] = cur[q];
       heat_solve_df<E>(f, z, nx, lane);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        const int i = lane * E + q;
         cur[q] = df_add_fast(df_scale2(z[q], 2.0f), -cur[q]);   // 0 beyond nx
-        if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_U, (long long)b * nx * nt + (long long)k * nx + i, nvar))
-          ub[(size_t)k * nx + i] = hd_to_double(cur[q]);
+        sl.u[k & 1][q][lane] = cur[q];
       }
+    } else if (k >= 2) {
+      take(k - 1);
     }
+    __syncthreads();
   }
-  __syncthreads();                    // u written
-  if (w == 0) {
-    // multipliers by backward substitution; the next step's u_hat and u loaded one ahead
-    const df64 dt_d = df64(a.dt);
-    df64 lam1[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) lam1[q] = zero;
-    bool in_range = true;
-    double xh[E], xu[E];
+  // warp 1 prepares dt r^k = dt (u_hat^k - u^k) (r^0 unscaled) into slot r[k & 1] and loads
+  // slice k - 1 for the next call
+  double ph[E], pu[E];
+  auto prep = [&](int k) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      xh[q] = (i < nx) ? uhb[(size_t)(nt - 1) * nx + i] : 0.0;
-      xu[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;
+      df64 v;
+      in_range &= df_split_trunc(ph[q] - pu[q], v.hi, v.lo);   // 0 beyond nx
+      const df64 sv = dt_d * v;
+      sl.r[k & 1][q][lane] = (k > 0) ? sv : v;
+      ph[q] = (i < nx && k >= 1) ? uhb[(size_t)(k - 1) * nx + i] : 0.0;
+      pu[q] = (i < nx && k >= 1) ? ub[(size_t)(k - 1) * nx + i] : 0.0;
     }
-    for (int k = nt - 1; k >= 1; --k) {
+  };
+  if (w == 1) {
+    if (nt >= 2) take(nt - 1);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      const int i = lane * E + q;
+      ph[q] = (i < nx) ? uhb[(size_t)(nt - 1) * nx + i] : 0.0;
+      pu[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;
+    }
+    prep(nt - 1);
+  }
+  __syncthreads();
+  // the multiplier chain: iteration k computes lambda^k (warp 0); warp 1 prepares dt r^{k-1}
+  // and stores lambda^{k+1}
+  df64 lam1[E];
+#pragma unroll
+  for (int q = 0; q < E; ++q) lam1[q] = zero;
+  for (int k = nt - 1; k >= 1; --k) {
+    if (w == 0) {
       df64 y[E];
 #pragma unroll
-      for (int q = 0; q < E; ++q) {
-        const int i = lane * E + q;
-        in_range &= df_split_trunc(xh[q] - xu[q], y[q].hi, y[q].lo);
-        xh[q] = (i < nx) ? uhb[(size_t)(k - 1) * nx + i] : 0.0;
-        xu[q] = (i < nx) ? ub[(size_t)(k - 1) * nx + i] : 0.0;
-      }
-#pragma unroll
-      for (int q = 0; q < E; ++q)
-        y[q] = hd_fma(dt_d, y[q], df_scale2(lam1[q], 2.0f));   // 0 beyond nx
+      for (int q = 0; q < E; ++q) y[q] = df_add_fast(sl.r[k & 1][q][lane], df_scale2(lam1[q], 2.0f));
       heat_solve_df<E>(f, y, nx, lane);
 #pragma unroll
       for (int q = 0; q < E; ++q) {
-        const int i = lane * E + q;
-        const df64 lk = df_sub_fast(y[q], lam1[q]);
-        if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + (long long)(k - 1) * nx + i, a.n_rows))
-          lb[a.off_pde + (size_t)(k - 1) * nx + i] = hd_to_double(lk);
-        lam1[q] = lk;
+        lam1[q] = df_sub_fast(y[q], lam1[q]);         // lambda^k, 0 beyond nx
+        sl.l[k & 1][q][lane] = lam1[q];
+      }
+    } else {
+      prep(k - 1);
+      if (k + 1 < nt) {
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          const int i = lane * E + q;
+          const double v = hd_to_double(sl.l[(k + 1) & 1][q][lane]);
+          if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + (long long)k * nx + i, a.n_rows))
+            lb[a.off_pde + (size_t)k * nx + i] = v;
+        }
       }
     }
-    // IC multipliers: r^0 + (2 lambda^1 - A lambda^1) / dt = r^0 + c2 lambda^1 + c3 (l + r),
-    // r^0 from the slice-0 values the last step loaded
-    df64 ll[E], lr[E], v0[E];
+    __syncthreads();
+  }
+  if (w == 0) {
+    // IC multipliers: r^0 + (2 lambda^1 - A lambda^1) / dt = r^0 + c2 lambda^1 + c3 (l + r)
+    df64 ll[E], lr[E];
     heat_neighbours_df<E>(lam1, ll, lr, nx, lane);
 #pragma unroll
-    for (int q = 0; q < E; ++q) in_range &= df_split_trunc(xh[q] - xu[q], v0[q].hi, v0[q].lo);
-#pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
+      const df64 r0 = sl.r[0][q][lane];
       if (i < nx)
-        lb[i] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, lam1[q], v0[q])));
+        lb[i] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, lam1[q], r0)));
     }
-    for (int k = lane; k < nt; k += 32) lb[a.off_mass + k] = 0.0;
-    for (int k = lane; k < nt - 1; k += 32) lb[a.off_energy + k] = 0.0;
-    in_range = __all_sync(kAll, in_range);
-    if (lane == 0) xc.ok0 = in_range;
   } else {
-    // the rows of slices 1 .. nt-1 from the written u, and the objective 1/2 |u_hat - u|^2
-    df64 sg = zero, sq = zero;
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      sg = df_add_fast(sg, cur[q]);
-      sq = hd_fma(cur[q], cur[q], sq);
-    }
-    const df64 sum_g = hd_warp_sum(sg);
-    df64 e_last = c.half_dx * hd_warp_sum(sq);   // energy of slice 0
-    float hmax = 0.0f;                  // IC rows and the mass row of slice 0 hold exactly
-    double obj = 0.0;
-    bool in_range = true;
-    double xh[E], xu[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int i = lane * E + q;
-      if (i < nx) {
-        const double r0 = uhb[i] - g[q];
-        obj = fma(r0, r0, obj);
-      }
-      xh[q] = (i < nx && nt > 1) ? uhb[(size_t)nx + i] : 0.0;
-      xu[q] = (i < nx && nt > 1) ? ub[(size_t)nx + i] : 0.0;
-    }
-    df64 prev[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) prev[q] = cur[q];
-    int nrow = 0;
-    for (int k = 1; k < nt; ++k) {
+    if (nt >= 2) {
 #pragma unroll
       for (int q = 0; q < E; ++q) {
         const int i = lane * E + q;
-        const double rd = xh[q] - xu[q];
-        obj = fma(rd, rd, obj);
-        in_range &= df_split_trunc(xu[q], cur[q].hi, cur[q].lo);
-        xh[q] = (i < nx && k + 1 < nt) ? uhb[(size_t)(k + 1) * nx + i] : 0.0;
-        xu[q] = (i < nx && k + 1 < nt) ? ub[(size_t)(k + 1) * nx + i] : 0.0;
+        const double v = hd_to_double(sl.l[1][q][lane]);           // lambda^1
+        if (i < nx && snap_in_bounds(SNAP_SITE_HEAT_LAM, a.off_pde + i, a.n_rows))
+          lb[a.off_pde + i] = v;
       }
-      df64 su, su2, sd2;
-      heat_slice_rows_df<E>(c, cur, prev, nx, lane, hmax, su, su2, sd2);
-      rs.su[nrow][lane] = su;
-      rs.su2[nrow][lane] = su2;
-      rs.sd2[nrow][lane] = sd2;
-      if (++nrow == 32) {
-        heat_rows_flush(c, sum_g, rs, 32, e_last, hmax, lane);
-        nrow = 0;
-      }
-#pragma unroll
-      for (int q = 0; q < E; ++q) prev[q] = cur[q];
     }
+    for (int k = lane; k < nt; k += 32) lb[a.off_mass + k] = 0.0;
+    for (int k = lane; k < nt - 1; k += 32) lb[a.off_energy + k] = 0.0;
     if (nrow > 0) heat_rows_flush(c, sum_g, rs, nrow, e_last, hmax, lane);
     hmax = hd_warp_max(hmax);
     obj = h_warp_sum(obj);
@@ -646,11 +704,11 @@ __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int la
     if (lane == 0) {
       xc.hmax = hmax;
       xc.obj = obj;
-      xc.ok1 = in_range;
+      xc.ok = in_range;
     }
   }
   __syncthreads();                    // multipliers and statistics done
-  if (!(xc.ok0 && xc.ok1)) return false;
+  if (!xc.ok) return false;
   if (w == 0 && lane == 0 && a.stats) {
     const double hmaxd = (double)xc.hmax;
     const double objd = 0.5 * xc.obj;
@@ -703,43 +761,51 @@ __device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int l
 #pragma unroll
     for (int q = 0; q < E; ++q) ok &= df_split_trunc(x[q], nxt[q].hi, nxt[q].lo);
   }
-  // gbar^k and u^{k-1} of the next step are loaded one iteration ahead
+  // Iteration k solves for b^k.  Off the chain it adds the dalpha term of step k + 1,
+  // b^{k+1} . 1/2 D2 (u^{k+1} + u^k) (pending from the iteration before; zero in the first), and
+  // splits gbar^{k-1}, u^{k-2} for the next iteration, whose loads were issued one earlier.
+  df64 yk[E], uk1[E], bp[E], sp[E];
   double xg[E], xu[E];
 #pragma unroll
   for (int q = 0; q < E; ++q) {
     const int i = lane * E + q;
-    xg[q] = (i < nx && nt > 1) ? gb[(size_t)(nt - 1) * nx + i] : 0.0;
-    xu[q] = (i < nx && nt > 1) ? ub[(size_t)(nt - 2) * nx + i] : 0.0;
+    ok &= df_split_trunc((i < nx && nt > 1) ? gb[(size_t)(nt - 1) * nx + i] : 0.0, yk[q].hi, yk[q].lo);
+    ok &= df_split_trunc((i < nx && nt > 1) ? ub[(size_t)(nt - 2) * nx + i] : 0.0, uk1[q].hi, uk1[q].lo);
+    xg[q] = (i < nx && nt > 2) ? gb[(size_t)(nt - 2) * nx + i] : 0.0;
+    xu[q] = (i < nx && nt > 2) ? ub[(size_t)(nt - 3) * nx + i] : 0.0;
+    bp[q] = zero;
+    sp[q] = zero;
   }
+  auto dalpha_term = [&]() {
+    df64 sl[E], sr[E];
+    heat_neighbours_df<E>(sp, sl, sr, nx, lane);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+      // 0 beyond nx (b, s and the neighbours are)
+      const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(sp[q], 2.0f));
+      dalpha = hd_fma(bp[q], cd2 * d2, dalpha);
+    }
+  };
   for (int k = nt - 1; k >= 1; --k) {
-    df64 y[E], cur[E];
+    df64 y[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) y[q] = hd_fma(dt_d, yk[q], df_scale2(b1[q], 2.0f));   // 0 beyond nx
+    heat_solve_df<E>(f, y, nx, lane);
+    dalpha_term();
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      ok &= df_split_trunc(xg[q], y[q].hi, y[q].lo);
-      ok &= df_split_trunc(xu[q], cur[q].hi, cur[q].lo);
-      xg[q] = (i < nx && k > 1) ? gb[(size_t)(k - 1) * nx + i] : 0.0;
-      xu[q] = (i < nx && k > 1) ? ub[(size_t)(k - 2) * nx + i] : 0.0;   // u^{k-2}
-    }
-#pragma unroll
-    for (int q = 0; q < E; ++q) y[q] = hd_fma(dt_d, y[q], df_scale2(b1[q], 2.0f));   // 0 beyond nx
-    heat_solve_df<E>(f, y, nx, lane);
-    // b^k . 1/2 D2 (u^k + u^{k-1})
-    df64 s[E], sl[E], sr[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      b1[q] = df_sub_fast(y[q], b1[q]);   // 0 beyond nx
-      s[q] = df_add_fast(nxt[q], cur[q]);
-    }
-    heat_neighbours_df<E>(s, sl, sr, nx, lane);
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      // 0 beyond nx (b^k, s and the neighbours are)
-      const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(s[q], 2.0f));
-      dalpha = hd_fma(b1[q], cd2 * d2, dalpha);
-      nxt[q] = cur[q];
+      sp[q] = df_add_fast(nxt[q], uk1[q]);            // u^k + u^{k-1}
+      nxt[q] = uk1[q];
+      ok &= df_split_trunc(xg[q], yk[q].hi, yk[q].lo);     // gbar^{k-1}
+      ok &= df_split_trunc(xu[q], uk1[q].hi, uk1[q].lo);   // u^{k-2}
+      xg[q] = (i < nx && k >= 3) ? gb[(size_t)(k - 2) * nx + i] : 0.0;
+      xu[q] = (i < nx && k >= 3) ? ub[(size_t)(k - 3) * nx + i] : 0.0;
+      b1[q] = df_sub_fast(y[q], b1[q]);               // b^k, 0 beyond nx
+      bp[q] = b1[q];
     }
   }
+  dalpha_term();                                       // step 1
   if (!__all_sync(kAll, ok)) return false;
   dalpha = hd_warp_sum(dalpha);
   double g0[E];
@@ -998,8 +1064,9 @@ __global__ void __launch_bounds__(64) k_heat_forward(HeatArgs a) {
   if (b >= a.B) return;
   if constexpr (E <= 8) {
     __shared__ HeatRowSums rs;
+    __shared__ HeatSlots<E> sl;
     __shared__ HeatXchg xc;
-    if (heat_forward_df<E>(a, b, lane, w, rs, xc)) return;
+    if (heat_forward_df<E>(a, b, lane, w, rs, sl, xc)) return;
   }
   if (w == 0) heat_forward_fp64<E>(a, b, lane);
 }
