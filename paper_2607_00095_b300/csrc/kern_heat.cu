@@ -727,11 +727,25 @@ __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int la
   return true;
 }
 
-// Adjoint of sample b in double-float (heat_backward_fp64's recurrences).  Returns false,
-// having written only values that the FP64 path overwrites, when a value leaves the
-// double-float range (bad samples and alpha included).
+// Hand-over slots of the adjoint block: dt gbar^k (warp 1 -> warp 0) and b^k (warp 0 -> warp 1).
 template <int E>
-__device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int lane) {
+struct HeatAdjSlots {
+  df64 y[2][E][32];
+  df64 b[2][E][32];
+  df64 dalpha;
+  int ok0, ok1;
+};
+
+// Adjoint of sample b in double-float (heat_backward_fp64's recurrences), by the two warps of
+// the block.  Warp 0 runs only the chain b^k = A^-1 (dt gbar^k + 2 b^{k+1}) - b^{k+1}; warp 1
+// prepares dt gbar^k one step ahead and adds the dalpha term b^{k+1} . 1/2 D2 (u^{k+1} + u^k)
+// one step behind, through HeatAdjSlots, one block barrier per step.  Both warps run the same
+// loops and return the same value: false, having written nothing, when a value leaves the
+// double-float range (bad samples and alpha included); the outputs are written after the last
+// barrier.
+template <int E>
+__device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int lane, int w,
+                                                 HeatAdjSlots<E> &sl) {
   const int nx = a.nx, nt = a.nt;
   const double *pg = a.params + (size_t)b * (nx + 1);
   const double alpha = pg[nx];
@@ -743,91 +757,117 @@ __device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int l
   double *gh = a.grad_uh + (size_t)b * nx * nt;
   double *gp = a.grad_params ? a.grad_params + (size_t)b * (nx + 1) : nullptr;
   const df64 zero(0.0f, 0.0f);
-  HeatFactorDF<E> f;
-  heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
   const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
   const df64 dt_d = df64(a.dt);
   const df64 cd2 = df64(0.5 / (a.dx * a.dx));
+  HeatFactorDF<E> f;
+  if (w == 0) heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
+  // warp 1 state: dt gbar of the next step and u^{k+1}, u^k, u^{k-1} around the pending term
   bool ok = true;
-  df64 b1[E], nxt[E], dalpha = zero;
-  {
-    double x[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-      const int i = lane * E + q;
-      b1[q] = zero;
-      x[q] = (i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0;   // u^k of the step below
-    }
-#pragma unroll
-    for (int q = 0; q < E; ++q) ok &= df_split_trunc(x[q], nxt[q].hi, nxt[q].lo);
-  }
-  // Iteration k solves for b^k.  Off the chain it adds the dalpha term of step k + 1,
-  // b^{k+1} . 1/2 D2 (u^{k+1} + u^k) (pending from the iteration before; zero in the first), and
-  // splits gbar^{k-1}, u^{k-2} for the next iteration, whose loads were issued one earlier.
-  df64 yk[E], uk1[E], bp[E], sp[E];
+  df64 dalpha = zero, ua[E], uc[E];
   double xg[E], xu[E];
-#pragma unroll
-  for (int q = 0; q < E; ++q) {
-    const int i = lane * E + q;
-    ok &= df_split_trunc((i < nx && nt > 1) ? gb[(size_t)(nt - 1) * nx + i] : 0.0, yk[q].hi, yk[q].lo);
-    ok &= df_split_trunc((i < nx && nt > 1) ? ub[(size_t)(nt - 2) * nx + i] : 0.0, uk1[q].hi, uk1[q].lo);
-    xg[q] = (i < nx && nt > 2) ? gb[(size_t)(nt - 2) * nx + i] : 0.0;
-    xu[q] = (i < nx && nt > 2) ? ub[(size_t)(nt - 3) * nx + i] : 0.0;
-    bp[q] = zero;
-    sp[q] = zero;
-  }
-  auto dalpha_term = [&]() {
-    df64 sl[E], sr[E];
-    heat_neighbours_df<E>(sp, sl, sr, nx, lane);
+  auto term = [&](const df64 (&bk)[E], const df64 (&s)[E]) {   // dalpha += b . cd2 D2 s
+    df64 sl_[E], sr_[E];
+    heat_neighbours_df<E>(s, sl_, sr_, nx, lane);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       // 0 beyond nx (b, s and the neighbours are)
-      const df64 d2 = df_sub_fast(df_add_fast(sl[q], sr[q]), df_scale2(sp[q], 2.0f));
-      dalpha = hd_fma(bp[q], cd2 * d2, dalpha);
+      const df64 d2 = df_sub_fast(df_add_fast(sl_[q], sr_[q]), df_scale2(s[q], 2.0f));
+      dalpha = hd_fma(bk[q], cd2 * d2, dalpha);
     }
   };
-  for (int k = nt - 1; k >= 1; --k) {
-    df64 y[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) y[q] = hd_fma(dt_d, yk[q], df_scale2(b1[q], 2.0f));   // 0 beyond nx
-    heat_solve_df<E>(f, y, nx, lane);
-    dalpha_term();
+  if (w == 1) {
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      sp[q] = df_add_fast(nxt[q], uk1[q]);            // u^k + u^{k-1}
-      nxt[q] = uk1[q];
-      ok &= df_split_trunc(xg[q], yk[q].hi, yk[q].lo);     // gbar^{k-1}
-      ok &= df_split_trunc(xu[q], uk1[q].hi, uk1[q].lo);   // u^{k-2}
-      xg[q] = (i < nx && k >= 3) ? gb[(size_t)(k - 2) * nx + i] : 0.0;
-      xu[q] = (i < nx && k >= 3) ? ub[(size_t)(k - 3) * nx + i] : 0.0;
-      b1[q] = df_sub_fast(y[q], b1[q]);               // b^k, 0 beyond nx
-      bp[q] = b1[q];
+      df64 v;
+      ok &= df_split_trunc((i < nx && nt > 1) ? gb[(size_t)(nt - 1) * nx + i] : 0.0, v.hi, v.lo);
+      sl.y[(nt - 1) & 1][q][lane] = dt_d * v;
+      ok &= df_split_trunc((i < nx) ? ub[(size_t)(nt - 1) * nx + i] : 0.0, uc[q].hi, uc[q].lo);
+      ua[q] = zero;
+      xg[q] = (i < nx && nt > 2) ? gb[(size_t)(nt - 2) * nx + i] : 0.0;
+      xu[q] = (i < nx && nt > 1) ? ub[(size_t)(nt - 2) * nx + i] : 0.0;
     }
   }
-  dalpha_term();                                       // step 1
-  if (!__all_sync(kAll, ok)) return false;
-  dalpha = hd_warp_sum(dalpha);
-  double g0[E];
+  __syncthreads();
+  df64 b1[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) g0[q] = (lane * E + q < nx) ? gb[lane * E + q] : 0.0;
-  df64 v0[E];
-  bool ok0 = true;
+  for (int q = 0; q < E; ++q) b1[q] = zero;
+  for (int k = nt - 1; k >= 1; --k) {
+    if (w == 0) {
+      df64 y[E];
 #pragma unroll
-  for (int q = 0; q < E; ++q) ok0 &= df_split_trunc(g0[q], v0[q].hi, v0[q].lo);
-  if (!__all_sync(kAll, ok0)) return false;
-  for (size_t i = lane; i < (size_t)nx * nt; i += 32) gh[i] = 0.0;
-  if (gp) {
+      for (int q = 0; q < E; ++q) y[q] = df_add_fast(sl.y[k & 1][q][lane], df_scale2(b1[q], 2.0f));
+      heat_solve_df<E>(f, y, nx, lane);
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        b1[q] = df_sub_fast(y[q], b1[q]);             // b^k, 0 beyond nx
+        sl.b[k & 1][q][lane] = b1[q];
+      }
+    } else {
+      // ua = u^{k+1}, uc = u^k; xg = gbar^{k-1}, xu = u^{k-1} (loaded one step ahead)
+      if (k + 1 < nt) {
+        df64 bk[E], s[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+          bk[q] = sl.b[(k + 1) & 1][q][lane];
+          s[q] = df_add_fast(ua[q], uc[q]);
+        }
+        term(bk, s);                                   // step k + 1
+      }
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        const int i = lane * E + q;
+        df64 v;
+        ok &= df_split_trunc(xg[q], v.hi, v.lo);
+        sl.y[(k - 1) & 1][q][lane] = dt_d * v;         // dt gbar^{k-1} (unused for k = 1)
+        ua[q] = uc[q];
+        ok &= df_split_trunc(xu[q], uc[q].hi, uc[q].lo);
+        xg[q] = (i < nx && k >= 3) ? gb[(size_t)(k - 2) * nx + i] : 0.0;
+        xu[q] = (i < nx && k >= 2) ? ub[(size_t)(k - 2) * nx + i] : 0.0;
+      }
+    }
+    __syncthreads();
+  }
+  // IC gradient (warp 0): gbar^0 + (2 b^1 - A b^1) / dt = gbar^0 + c2 b^1 + c3 (l + r)
+  double gpv[E];
+  if (w == 0) {
     df64 ll[E], lr[E];
     heat_neighbours_df<E>(b1, ll, lr, nx, lane);
 #pragma unroll
     for (int q = 0; q < E; ++q) {
       const int i = lane * E + q;
-      // gbar^0 + (2 b^1 - A b^1) / dt = gbar^0 + c2 b^1 + c3 (l + r)
-      if (i < nx)
-        gp[i] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, b1[q], v0[q])));
+      df64 v0;
+      ok &= df_split_trunc((i < nx) ? gb[i] : 0.0, v0.hi, v0.lo);
+      gpv[q] = hd_to_double(hd_fma(c.c3, df_add_fast(ll[q], lr[q]), hd_fma(c.c2, b1[q], v0)));
     }
-    if (lane == 0) gp[nx] = hd_to_double(dalpha);
+    ok = __all_sync(kAll, ok);
+    if (lane == 0) sl.ok0 = ok;
+  } else {
+    if (nt >= 2) {
+      df64 bk[E], s[E];
+#pragma unroll
+      for (int q = 0; q < E; ++q) {
+        bk[q] = sl.b[1][q][lane];                      // b^1
+        s[q] = df_add_fast(ua[q], uc[q]);              // u^1 + u^0
+      }
+      term(bk, s);                                     // step 1
+    }
+    dalpha = hd_warp_sum(dalpha);
+    ok = __all_sync(kAll, ok);
+    if (lane == 0) {
+      sl.ok1 = ok;
+      sl.dalpha = dalpha;
+    }
+  }
+  __syncthreads();
+  if (!(sl.ok0 && sl.ok1)) return false;               // the same verdict in both warps
+  for (size_t i = threadIdx.x; i < (size_t)nx * nt; i += 64) gh[i] = 0.0;
+  if (gp && w == 0) {
+#pragma unroll
+    for (int q = 0; q < E; ++q)
+      if (lane * E + q < nx) gp[lane * E + q] = gpv[q];
+    if (lane == 0) gp[nx] = hd_to_double(sl.dalpha);
   }
   return true;
 }
@@ -1054,9 +1094,9 @@ __device__ __noinline__ void heat_backward_fp64(const HeatArgs &a, int b, int la
   }
 }
 
-// One sample per block (the samples spread over every SM): the double-float chains (two warps
-// in the forward, one in the adjoint), or the FP64 chain in warp 0 for a sample whose values
-// leave the double-float range (and for E > 8, where the double-float arrays would spill).
+// One sample per block of two warps (the samples spread over every SM): the double-float
+// chains, or the FP64 chain in warp 0 for a sample whose values leave the double-float range
+// (and for E > 8, where the double-float arrays would spill).
 template <int E>
 __global__ void __launch_bounds__(64) k_heat_forward(HeatArgs a) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1072,14 +1112,15 @@ __global__ void __launch_bounds__(64) k_heat_forward(HeatArgs a) {
 }
 
 template <int E>
-__global__ void __launch_bounds__(32) k_heat_backward(HeatArgs a) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(64) k_heat_backward(HeatArgs a) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int b = blockIdx.x;
   if (b >= a.B) return;
   if constexpr (E <= 8) {
-    if (heat_backward_df<E>(a, b, lane)) return;
+    __shared__ HeatAdjSlots<E> sl;
+    if (heat_backward_df<E>(a, b, lane, w, sl)) return;
   }
-  heat_backward_fp64<E>(a, b, lane);
+  if (w == 0) heat_backward_fp64<E>(a, b, lane);
 }
 
 template <int E>
@@ -1087,7 +1128,7 @@ void heat_launch(int kind, const HeatArgs &a, cudaStream_t s) {
   const unsigned blocks = (unsigned)(((long long)a.B * 32 + 127) / 128);
   if (kind == 0) k_heat_forward<E><<<(unsigned)a.B, 64, 0, s>>>(a);
   else if (kind == 1) k_heat_residual<E><<<blocks, 128, 0, s>>>(a);
-  else k_heat_backward<E><<<(unsigned)a.B, 32, 0, s>>>(a);
+  else k_heat_backward<E><<<(unsigned)a.B, 64, 0, s>>>(a);
 }
 
 cudaError_t heat_dispatch(int kind, const HeatArgs &a, cudaStream_t s) {
