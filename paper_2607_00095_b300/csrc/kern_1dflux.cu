@@ -141,6 +141,32 @@ __device__ __forceinline__ double fx_slice_sum(const double *row, int nx, int r,
   return S;
 }
 
+// sum_i g[i] over the full warp (lane l takes i = l, l + 32, ...) in the same split / TwoSum
+// arithmetic, the lane sums combined by a fixed butterfly in double-float: the same bits in
+// every warp that computes it.  A row with a value outside the split range is summed in FP64
+// (warp-uniform).
+__device__ __forceinline__ double fx_row_sum32(const double *g, int nx, int lane) {
+  float sh = 0.0f, se = 0.0f;
+  int ok = 1;
+  for (int i = lane; i < nx; i += 32) {
+    float h, l;
+    ok &= df_split_trunc(g[i], h, l);
+    const float t = sh + h, bb = t - sh;
+    se += ((sh - (t - bb)) + (h - bb)) + l;
+    sh = t;
+  }
+  if (!__all_sync(FULL, ok)) {
+    double t = 0.0;
+    for (int i = lane; i < nx; i += 32) t += g[i];
+    return fx_warp_sum(t);
+  }
+  df64 v = df_fast_two_sum(sh, se);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = v + df64(__shfl_xor_sync(FULL, v.hi, o), __shfl_xor_sync(FULL, v.lo, o));
+  return (double)v.hi + (double)v.lo;
+}
+
 __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int lane) {
   const int q = lane >> 2, r = lane & 3;
   const long long s = wid * 8 + q;
@@ -168,10 +194,7 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
     const int bq = __shfl_sync(FULL, b, qq * 4);
     if (!__shfl_sync(FULL, live ? 1 : 0, qq * 4)) break;   // live slices are a prefix
     if (bq != cb) {
-      const double *g = a.g + (size_t)bq * nx;
-      double t = 0.0;
-      for (int i = lane; i < nx; i += 32) t += g[i];
-      cur = fx_warp_sum(t);
+      cur = fx_row_sum32(a.g + (size_t)bq * nx, nx, lane);
       cb = bq;
     }
     if (q == qq) Gs = cur;
