@@ -9,9 +9,10 @@
 // ordered (D, M, N) and nx >= 3, A A^T = [[1, dx, 0], [dx, nx dx^2, 0], [0, 0, 2]] (the
 // Neumann row sums to zero and misses x_0), solved in closed form per slice.
 //
-// Four lanes per slice (eight slices per warp): the sum of u_hat, the 3x3 solve on one lane
-// of the slice, the write u_i = u_hat_i - dx lambda_M (- lambda_D at i = 0, -+ lambda_N at the
-// right pair): two FP64 operations per element (FP64 is the scarce pipe on this GPU).  The
+// Four lanes per slice (eight slices per warp): the sum of u_hat on the FP32 and integer pipes
+// (s4_slice_sum), the 3x3 solve on one lane of the slice, the write u_i = u_hat_i - dx
+// lambda_M (- lambda_D at i = 0, -+ lambda_N at the right pair): one FP64 operation per element
+// (FP64 is the scarce pipe on this GPU).  The
 // statistics come from the step's closed form.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -69,13 +70,7 @@ k1dbc_forward(int B, int nt, int nx, double dx, double inv_det, const double *__
   const double *row = uh + (size_t)(live ? s : 0) * nx;
   double *out = u + (size_t)(live ? s : 0) * nx;
   // F at (u_hat, 0): the rows (the Lagrangian gradient is zero there)
-  double S = 0.0;
-  if (live) {
-#pragma unroll 8
-    for (int i = r; i < nx; i += 4) S += row[i];
-  }
-  S += __shfl_xor_sync(FULL, S, 1);
-  S += __shfl_xor_sync(FULL, S, 2);
+  const double S = s4_slice_sum(row, nx, r, live);
   double f0 = 0.0, lD = 0.0, lM = 0.0, lN = 0.0;
   double uL = 0.0, m0 = 0.0, u0v = 0.0, ua = 0.0, ub = 0.0;
   if (live && r == 0) {
@@ -152,12 +147,7 @@ k1dbc_backward(int B, int nt, int nx, double dx, double inv_det, const double *_
   const int b = !live ? 0 : nsl < (1LL << 31) ? (int)((unsigned)s / (unsigned)nt) : (int)(s / nt);
   const double *row = gu + (size_t)(live ? s : 0) * nx;
   double *out = gh + (size_t)(live ? s : 0) * nx;
-  double p0 = 0.0;
-  if (live)
-    for (int i = r; i < nx; i += 4) p0 += row[i];
-  double S = p0;
-  S += __shfl_xor_sync(FULL, S, 1);
-  S += __shfl_xor_sync(FULL, S, 2);
+  const double S = s4_slice_sum(row, nx, r, live);
   double lD = 0.0, lM = 0.0, lN = 0.0;
   const bool bad = live && fst && fst[b].status != SNAP_SAMPLE_OK;
   if (live && r == 0) {

@@ -24,7 +24,6 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include "df64.cuh"
 #include "sample_1d.cuh"
 #include "kern_1dflux.h"
 #include "snap_internal.h"
@@ -104,43 +103,6 @@ __device__ __forceinline__ void put_stat(BlockStat *dst, double hinf, double obj
 }
 
 // Mass slices k = K+1..nt-1: four lanes per slice (eight slices per warp).
-// sum_i row[i] of a mass slice over its four lanes (lane r takes i = r, r + 4, ...), on the FP32
-// and integer pipes: every value split into a float pair by integer operations (df_split_trunc,
-// |x - hi - lo| < 2^-46 |x|), the pairs summed by TwoSum with the errors carried, the four lane
-// sums combined in double-float.  A slice with a value outside the split range (|x| outside
-// [2^-74, 2^57] and not zero, or non-finite) is summed in FP64 instead; the four lanes of a
-// slice agree on the path.  The FP64 pipe (2 lanes per clock per SM on B300) otherwise spends
-// one addition per element here.
-__device__ __forceinline__ double fx_slice_sum(const double *row, int nx, int r, bool live) {
-  float sh = 0.0f, se = 0.0f;
-  int ok = 1;
-  if (live) {
-#pragma unroll 8
-    for (int i = r; i < nx; i += 4) {
-      float h, l;
-      ok &= df_split_trunc(row[i], h, l);
-      const float t = sh + h, bb = t - sh;
-      se += ((sh - (t - bb)) + (h - bb)) + l;
-      sh = t;
-    }
-  }
-  ok &= __shfl_xor_sync(FULL, ok, 1);
-  ok &= __shfl_xor_sync(FULL, ok, 2);
-  df64 v = df_fast_two_sum(sh, se);
-  v = v + df64(__shfl_xor_sync(FULL, v.hi, 1), __shfl_xor_sync(FULL, v.lo, 1));
-  v = v + df64(__shfl_xor_sync(FULL, v.hi, 2), __shfl_xor_sync(FULL, v.lo, 2));
-  double S = (double)v.hi + (double)v.lo;
-  if (__any_sync(FULL, !ok)) {         // rare, warp-uniform: the FP64 sums of the warp's slices
-    double T = 0.0;
-    if (live)
-      for (int i = r; i < nx; i += 4) T += row[i];
-    T += __shfl_xor_sync(FULL, T, 1);
-    T += __shfl_xor_sync(FULL, T, 2);
-    if (!ok) S = T;
-  }
-  return S;
-}
-
 // sum_i g[i] over the full warp (lane l takes i = l, l + 32, ...) in the same split / TwoSum
 // arithmetic, the lane sums combined by a fixed butterfly in double-float: the same bits in
 // every warp that computes it.  A row with a value outside the split range is summed in FP64
@@ -185,7 +147,7 @@ __device__ __forceinline__ void flux_mass(const FluxArgs &a, long long wid, int 
   }
   const size_t off = ((size_t)b * a.nt + k) * nx;
   const double *row = a.uh + off;
-  const double S = fx_slice_sum(row, nx, r, live);
+  const double S = s4_slice_sum(row, nx, r, live);
   // sum g of each distinct sample among the warp's eight slices (usually one or two): a
   // full-warp sum, the same bits whichever warp computes it
   double Gs = 0.0, cur = 0.0;
@@ -420,7 +382,7 @@ __device__ __forceinline__ void flux_mass_bwd(const FluxBwdArgs &a, long long wi
   const int b = live ? (int)(s / nm) : 0, k = live ? a.K + 1 + (int)(s % nm) : 0;
   const size_t off = ((size_t)b * a.nt + k) * nx;
   const double *row = a.gu + off;
-  const double S = fx_slice_sum(row, nx, r, live);
+  const double S = s4_slice_sum(row, nx, r, live);
   if (!live) return;
   const bool bad = a.fst && a.fst[b].status != SNAP_SAMPLE_OK;
   const double mean = S / (double)nx;

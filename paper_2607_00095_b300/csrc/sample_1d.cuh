@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "df64.cuh"
 #include "snap_internal.h"
 
 namespace {
@@ -194,6 +195,43 @@ __device__ __forceinline__ void s1_param_grad(const Geom1D &g, const double *__r
     out[i] = bad ? NAN : v;
   }
   if (lane == 0) out[g.p_rate] = bad ? NAN : sr;
+}
+
+// sum_i row[i] of a slice over its four lanes (four lanes per slice, eight slices per warp) (lane r takes i = r, r + 4, ...), on the FP32
+// and integer pipes: every value split into a float pair by integer operations (df_split_trunc,
+// |x - hi - lo| < 2^-46 |x|), the pairs summed by TwoSum with the errors carried, the four lane
+// sums combined in double-float.  A slice with a value outside the split range (|x| outside
+// [2^-74, 2^57] and not zero, or non-finite) is summed in FP64 instead; the four lanes of a
+// slice agree on the path.  The FP64 pipe (2 lanes per clock per SM on B300) otherwise spends
+// one addition per element here.
+__device__ __forceinline__ double s4_slice_sum(const double *row, int nx, int r, bool live) {
+  float sh = 0.0f, se = 0.0f;
+  int ok = 1;
+  if (live) {
+#pragma unroll 8
+    for (int i = r; i < nx; i += 4) {
+      float h, l;
+      ok &= df_split_trunc(row[i], h, l);
+      const float t = sh + h, bb = t - sh;
+      se += ((sh - (t - bb)) + (h - bb)) + l;
+      sh = t;
+    }
+  }
+  ok &= __shfl_xor_sync(0xffffffffu, ok, 1);
+  ok &= __shfl_xor_sync(0xffffffffu, ok, 2);
+  df64 v = df_fast_two_sum(sh, se);
+  v = v + df64(__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1));
+  v = v + df64(__shfl_xor_sync(0xffffffffu, v.hi, 2), __shfl_xor_sync(0xffffffffu, v.lo, 2));
+  double S = (double)v.hi + (double)v.lo;
+  if (__any_sync(0xffffffffu, !ok)) {         // rare, warp-uniform: the FP64 sums of the warp's slices
+    double T = 0.0;
+    if (live)
+      for (int i = r; i < nx; i += 4) T += row[i];
+    T += __shfl_xor_sync(0xffffffffu, T, 1);
+    T += __shfl_xor_sync(0xffffffffu, T, 2);
+    if (!ok) S = T;
+  }
+  return S;
 }
 
 }  // namespace
