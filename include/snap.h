@@ -315,7 +315,9 @@ SNAP_API snap_status snap_pcfm_workspace_size(snap_problem_t p, int B, size_t *b
  * model is replaced by the analytic velocity v(u, tau) = (x1 - u_0) + sigma0 (1 - tau) xi
  * (the straight-path OT velocity from the prior sample u_0 to the data sample x1, plus a
  * decaying perturbation along xi).
- *   u0, x1, xi: device [B][n_vars] (16-byte aligned); params as snap_project.
+ *   u0, x1, xi: device [B][n_vars] (16-byte aligned); params as snap_project.  With this
+ *   velocity u_0 cancels from the shoot after the pull-back (u_hat_1 = tau u_1 + (1 - tau) x1
+ *   + sigma0 (1 - tau)^2 xi), so u0 is validated but not read.
  *   u: device [B][n_vars] out: u_1 of the last step (= the sample at tau = 1); it also holds
  *   the running u_1 between steps.  lambda, stats: of the last projection.
  * Asynchronous on stream, no allocation or synchronisation (capturable in a CUDA graph).
