@@ -2,7 +2,7 @@
 heat-equation constraint operator, Appendix A "Heat Equation Problems"; the energy-evolution
 identity of the appendix "Energy Evolution Constraint") -- TEST INFRASTRUCTURE ONLY.
 
-Discretisation (reading R26; the paper gives no stencil or time scheme):
+Discretisation (the paper gives no stencil or time scheme; the consistent reading of its rows):
   x_i = i dx on the periodic [0, 2 pi), dx = 2 pi / nx;  t_k = k dt, dt = 1 / (nt - 1).
   D2 v_i = (v_{i+1} - 2 v_i + v_{i-1}) / dx^2,  D+ v_i = (v_{i+1} - v_i) / dx  (periodic).
 Rows, in this order (per sample, params = [g_0 .. g_{nx-1}, alpha]):

@@ -70,7 +70,7 @@ typedef struct {
   int max_corrections;
   int split_components;
   double w_keep;
-  int restore;          /* 1: keep grad_u L = 0 along the iteration (reading R25, start u_hat) */
+  int restore;          /* 1: keep grad_u L = 0 along the iteration (start u_hat) */
 } ora_opts;
 
 typedef struct {
@@ -437,11 +437,11 @@ static void stationary_u(const comp_t *c, const double *uh, const double *lam, d
 
 /* Newton-KKT on one component.  u holds u0 on entry and the result on exit.
  *
- * restore = 0 (reading R14): the primal-dual iterate (u, lam) moves along the Newton-KKT
+ * restore = 0 (primal-dual): the iterate (u, lam) moves along the Newton-KKT
  * step of Appendix B, (u, lam) + t (du, dlam).
- * After the stopping test one polishing step is taken (reading R27, below).
+ * After the stopping test one polishing step is taken (below).
  *
- * restore = 1 (reading R25, used when the iteration starts at u0 = u_hat): the same Newton-KKT
+ * restore = 1 (used when the iteration starts at u0 = u_hat): the same Newton-KKT
  * step and line search, but every trial point is (u(lam_t), lam_t) with lam_t = lam + t dlam
  * and u(lam) = argmin_u L(u, lam) (stationary_u), so grad_u L = 0 along the whole iteration
  * and the Newton-KKT step reduces to S dlam = h with S = J W^-1 J^T.  The start u = u_hat,
@@ -530,7 +530,7 @@ static void newton_component(const comp_t *c, const double *uh, const double *b,
     res = norm_inf(F, N);
     st->iters = it + 1;
   }
-  /* Polishing step (reading R27): the stopping test bounds ||F||, and the multipliers only
+  /* Polishing step: the stopping test bounds ||F||, and the multipliers only
    * through the conditioning of the KKT matrix, which is large on slices whose boundary circle
    * is nearly degenerate; one more full Newton-KKT step leaves them at the rounding level.  It
    * is kept when ||F||_inf does not increase (and, with restore, W stays positive); it is not

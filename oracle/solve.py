@@ -69,8 +69,8 @@ def project(S, b, u_hat, u0=None, nthreads=0, **opts):
     if u0 is not None:
         u0 = np.ascontiguousarray(np.atleast_2d(u0).reshape(B, -1), np.float64)
         u0p = _p(u0, C.c_double)
-    # R25 (u kept stationary) for the projection's own start u0 = u_hat; an explicit start
-    # point u0 takes the primal-dual iteration of R14
+    # u kept stationary for the projection's own start u0 = u_hat; an explicit start point u0
+    # takes the primal-dual iteration
     opts.setdefault("restore", 0 if u0 is not None else 1)
     o = default_opts(**opts)
     L.ora_project_batch(S.n, S.m, _p(S.a_ptr, C.c_int), _p(S.a_col, C.c_int),

@@ -402,9 +402,8 @@ DF_INL void slice_newton_phase(const SliceIn<T> &d, const SliceIn<L> &dl, SliceZ
   }
 }
 
-// The whole iteration in one precision T (FP64 reference path), with the polishing step of
-// reading R27 (one more Newton step after the stopping test, kept when ||F||_inf does not
-// increase).
+// The whole iteration in one precision T (FP64 reference path), with the polishing step (one
+// more Newton step after the stopping test, kept when ||F||_inf does not increase).
 template <class T>
 DF_INL SliceResult slice_newton(const SliceIn<T> &d, SliceZ<T> &z, SliceEval<T> &e,
                                            const SolverOpts &o) {
@@ -547,15 +546,14 @@ DF_INL void slice_newton_h(const SliceIn<T> &d, const SliceIn<float> &d32, Slice
   }
 }
 
-// Polishing step after the stopping test (reading R27): the test bounds ||h||, and the
-// multipliers only through the conditioning of S, which is large on slices whose boundary
-// circle is nearly degenerate (c_k ~ 1e-6: S ~ 1e7 there).  One more Newton step leaves the
-// multipliers at the rounding level.  S is first factored in float at the float image of z:
-// when its pivots over the rows present are within a factor 1e3 of each other and its
-// multipliers l are below 1e2 (S well conditioned), the step is solved in float against the
-// double-float residual (one more step of iterative refinement, error factor ~ kappa 2^-24);
-// otherwise S is assembled, factored and solved in double-float.  The step is kept when it
-// does not increase ||h||_inf and leaves W positive.
+// Polishing step after the stopping test: the test bounds ||h||, and the multipliers only
+// through the conditioning of S, which is large on slices whose boundary circle is nearly
+// degenerate (c_k ~ 1e-6: S ~ 1e7 there).  One more Newton step on the multipliers leaves them
+// at the rounding level.  S is first factored in float at the float image of z: when its
+// pivots over the rows present are within a factor 1e3 of each other and its multipliers l are
+// below 1e2 (S well conditioned), the multipliers are already within ~1e3 ||F|| of converged
+// and no step is taken; otherwise S is assembled, factored and solved in double-float, and
+// the step is kept when it does not increase ||h||_inf and leaves W positive.
 DF_INL void slice_polish(const SliceIn<df64> &d, const SliceIn<float> &d32, SliceZ<df64> &z,
                          SliceH<df64> &e) {
   const df64 zero(0.0f, 0.0f), one(1.0f, 0.0f);
@@ -574,14 +572,11 @@ DF_INL void slice_polish(const SliceIn<df64> &d, const SliceIn<float> &d32, Slic
     const float lmax = fmaxf(fabsf(ff.l10), fmaxf(fabsf(ff.l20), fabsf(ff.l21)));
     cheap = dmax <= 1e3f * dmin && lmax <= 1e2f;
   }
+  // a well-conditioned S: the multipliers at the stopping point are within cond(S) ||F|| of
+  // converged, far inside their tolerance, and the step is not taken
+  if (cheap) return;
   df64 dlm, dle, dlb;
-  if (cheap) {
-    float xm, xe, xb;
-    ldl3_solve(ff, hm ? e.hm.hi : 0.0f, he ? e.he.hi : 0.0f, hb ? e.hb.hi : 0.0f, xm, xe, xb);
-    dlm = df64(xm, 0.0f);
-    dle = df64(xe, 0.0f);
-    dlb = df64(xb, 0.0f);
-  } else {
+  {
     df64 s00, s01, s02, s11, s12, s22;
     slice_schur(d, z, e.su, e.su2, one / e.alpha, one / e.beta, s00, s01, s02, s11, s12, s22);
     Ldl3<df64> f;

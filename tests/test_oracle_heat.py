@@ -1,5 +1,5 @@
 """Pins of the heat-equation oracle (oracle/heat.py: IC, mass, Crank-Nicolson PDE residual and
-energy-evolution rows; reading R26) against what the mathematics fixes: the closed-form
+energy-evolution rows, Crank-Nicolson discretisation) against what the mathematics fixes: the closed-form
 Crank-Nicolson decay of a single Fourier mode, the implied mass and energy rows (summation by
 parts), the generic dense Newton-KKT on the same active rows, stationarity with a
 finite-difference Jacobian, and central differences of the adjoint."""

@@ -190,11 +190,11 @@ def test_family_a_matches_closed_form_small_1d_workload():
     assert (st["status"] == 0).all() and (st["kkt_inf"] <= 1e-10).all()
     np.testing.assert_allclose(u, ue, rtol=0, atol=1e-9)
     # converged to the rounding floor, u and lambda agree to ~1e-13 (u = W^-1 (u_hat - A^T lam)
-    # under R25 rounds to within a few hundred ulps of the closed form's arithmetic)
+    # with u kept stationary rounds to within a few hundred ulps of the closed form's arithmetic)
     u, lam, st, S, b = solve.project_1d("A", nx, nt, pr, uh, tol_kkt=1e-13)
     assert (st["status"] == 0).all()
     np.testing.assert_allclose(u, ue, rtol=0, atol=3e-13)
-    # the primal-dual iteration of R14 (explicit start u0 = u_hat) reaches the same point
+    # the primal-dual iteration (explicit start u0 = u_hat) reaches the same point
     u2, lam2, st2, _, _ = solve.project_1d("A", nx, nt, pr, uh, u0=uh, tol_kkt=1e-13)
     assert (st2["status"] == 0).all()
     np.testing.assert_allclose(u2, ue, rtol=0, atol=3e-13)
