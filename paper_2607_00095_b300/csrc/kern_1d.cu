@@ -66,8 +66,10 @@ __global__ void k1d_params(Geom1D g, int B, const double *__restrict__ params,
                            double *__restrict__ bwd_gp, const snap_stats *__restrict__ bwd_st) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  // a kernel launched as this one's programmatic dependent may start now (it waits for this
-  // kernel's completion before it reads anything written here)
+  // launched as a programmatic dependent of the stream's previous kernel: wait for it to
+  // complete before touching memory; only then may this kernel's own dependent start (it
+  // reads its inputs before its own wait, so every kernel before this one must be complete)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (warp >= B) return;
   const double *pg = params + (size_t)warp * g.n_params;
@@ -97,8 +99,10 @@ __global__ void k_finalize_stats(int B, int nblk, const BlockStat *__restrict__ 
                                  snap_stats *__restrict__ out) {
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  // launched as a programmatic dependent of the tile kernel: wait for its statistics
+  // launched as a programmatic dependent of the tile kernel: wait for its statistics; the
+  // next kernel (a programmatic dependent that waits before it touches memory) may then launch
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (warp >= B) return;
   (void)tol_h_ptr;
   s1_finalize<false>(bs + (size_t)warp * nblk, nblk, tol_h, out + warp, lane);
@@ -759,6 +763,26 @@ size_t ws_bytes_1d(const snap_problem *p, int B) {
 
 static int warps_blocks(int nwarps) { return (nwarps * 32 + 127) / 128; }
 
+// k1d_params as a programmatic dependent of the stream's previous kernel: its launch overlaps
+// that kernel's tail, and it waits for that kernel's completion before its first access
+static void launch_params(const Geom1D &g, int B, const double *params, SampleDerived *sd,
+                          const double *ic_uh, double *ic_u, double *ic_lam, BlockStat *ic_bst,
+                          double tol_kkt, double *bwd_gh, BwdContrib *bwd_contrib,
+                          double *bwd_gp, const snap_stats *bwd_st, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)warps_blocks(B));
+  cfg.blockDim = dim3(128);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k1d_params, g, B, params, sd, ic_uh, ic_u, ic_lam, ic_bst, tol_kkt,
+                     bwd_gh, bwd_contrib, bwd_gp, bwd_st);
+}
+
 
 cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
                               const double *params, const double *u0, double *u, double *lambda,
@@ -768,9 +792,8 @@ cudaError_t launch_1d_forward(const snap_problem *p, int B, const double *u_hat,
   Ws1D w = carve_1d(p, B, ws);
   int launches = 0;
   const bool mixed = path == SNAP_PATH_MIXED;
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, u_hat, mixed ? u : nullptr,
-                                             lambda, w.bst, o.tol_kkt, nullptr, nullptr, nullptr,
-                                             nullptr);
+  launch_params(g, B, params, w.sd, u_hat, mixed ? u : nullptr, lambda, w.bst, o.tol_kkt,
+                nullptr, nullptr, nullptr, nullptr, s);
   launches++;
   if (mixed) {
     const int pid = snap_prof_begin(s, "k1d_mixed");
@@ -804,8 +827,8 @@ cudaError_t launch_1d_residual(const snap_problem *p, int B, const double *u,
                                cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
-                                             nullptr, 0.0, nullptr, nullptr, nullptr, nullptr);
+  launch_params(g, B, params, w.sd, nullptr, nullptr, nullptr, nullptr, 0.0, nullptr, nullptr,
+                nullptr, nullptr, s);
   SNAP_DISPATCH_NPL(g.nx, launch_residual, g, B, u, params, w.sd, h, w.smax, s);
   int launches = 2;
   if (h_inf) {
@@ -822,9 +845,8 @@ cudaError_t launch_1d_backward(const snap_problem *p, int B, const double *grad_
                                double *grad_params, void *ws, cudaStream_t s) {
   const Geom1D &g = p->g1;
   Ws1D w = carve_1d(p, B, ws);
-  k1d_params<<<warps_blocks(B), 128, 0, s>>>(g, B, params, w.sd, nullptr, nullptr, nullptr,
-                                             nullptr, 0.0, grad_u_hat, w.contrib, grad_params,
-                                             stats);
+  launch_params(g, B, params, w.sd, nullptr, nullptr, nullptr, nullptr, 0.0, grad_u_hat,
+                w.contrib, grad_params, stats, s);
   const int pid = snap_prof_begin(s, "k1d_bwd_mixed");
   launch_1d_bwd_mixed(g, B, grad_u, u, lambda, params, stats, w.sd,
                       grad_u_hat, grad_params, w.contrib, s);

@@ -61,6 +61,34 @@ __device__ __forceinline__ void tb_acc_prod(float &s, float &e, float xh, float 
   s = t;
 }
 
+// L2 residency hints for the adjoint tile: u and dL/du are read twice (the sums of phase 1,
+// the write-back of phase 3) and the whole batch's u and dL/du are in flight at once, so the
+// first reads keep their lines (evict_last), the second reads and the dL/du_hat stores mark
+// theirs for early eviction (evict_first): the outputs stream through L2 without pushing out
+// inputs that other tiles have still to re-read.
+__device__ __forceinline__ unsigned long long tb_policy_keep() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long tb_policy_drop() {
+  unsigned long long p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ double2 tb_ld2(const double *p, unsigned long long pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+               : "=d"(v.x), "=d"(v.y)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ void tb_st2(double *p, double2 v, unsigned long long pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x),
+               "d"(v.y), "l"(pol)
+               : "memory");
+}
+
 __device__ __forceinline__ df64 tb_df_pow(df64 x, int k) {
   df64 r(1.0f, 0.0f);
   while (k > 0) {
@@ -217,6 +245,7 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
   const int r = lane & 3;
   const int nx = g.nx, ih = g.ih;
   const df64 dxd(g.dx);
+  const unsigned long long pol_drop = tb_policy_drop();
   // ---------------- phase 1: sums over the interior ----------------
   df64 mg(0.0f, 0.0f), mug(0.0f, 0.0f), mu(0.0f, 0.0f), muu(0.0f, 0.0f);
   int mok = 1;
@@ -303,8 +332,8 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int i = i0 + 8 * c;
-        vu[c] = (i < nx) ? *reinterpret_cast<const double2 *>(urow + i) : make_double2(0.0, 0.0);
-        vg[c] = (i < nx) ? *reinterpret_cast<const double2 *>(grow + i) : make_double2(0.0, 0.0);
+        vu[c] = (i < nx) ? tb_ld2(urow + i, pol_drop) : make_double2(0.0, 0.0);
+        vg[c] = (i < nx) ? tb_ld2(grow + i, pol_drop) : make_double2(0.0, 0.0);
       }
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
@@ -314,7 +343,7 @@ __device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long lo
         double2 w;
         w.x = fma(vg[c].x, b0 ? iwb : iw, fma(vu[c].x, b0 ? kxb : kx, b0 ? k0b : k0));
         w.y = fma(vg[c].y, b1 ? iwb : iw, fma(vu[c].y, b1 ? kxb : kx, b1 ? k0b : k0));
-        *reinterpret_cast<double2 *>(out + i) = w;
+        tb_st2(out + i, w, pol_drop);
       }
     }
   }
