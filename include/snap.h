@@ -169,7 +169,8 @@ enum {
 
 typedef struct {
   int family;          /* snap_family */
-  int nx;              /* 1-D: points per slice (even, 4..512); 2-D: N (even, >= 4) */
+  int nx;              /* 1-D: points per slice (even, 4..512); 2-D: N (even, 4..64 in this
+                          build; the uneven batch takes 4, 8, 16, 32 and 64) */
   int ny;              /* 2-D: must equal nx; 1-D: ignored */
   int nt;              /* 1-D: time slices; 2-D: frames (>= 2) */
   unsigned rows;       /* 1-D: SNAP_ROW_* mask (IC required); 0 = family default */
@@ -398,7 +399,8 @@ SNAP_API snap_status snap_batch_set_group_lanes(snap_batch_t b, const int *lanes
 /* Host arrays probs[n_problems], inst_problem[n_inst]; the problems must outlive the batch.
  * Allocates the batch's device tables on the current device (bind and project use it).
  * Errors: INVALID_ARG (null arrays, index out of range, n_inst < 0), UNSUPPORTED (a family
- * other than A, B, C), NO_MEMORY / CUDA (device allocation). */
+ * other than A, B, C, or a family C grid side other than 4, 8, 16, 32, 64), NO_MEMORY / CUDA
+ * (device allocation). */
 SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *probs, int n_inst,
                                        const int *inst_problem, snap_batch_t *out);
 SNAP_API void snap_batch_destroy(snap_batch_t b);

@@ -41,7 +41,7 @@ def build(force=False, verbose=False, bounds_check=False):
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     objdir = os.path.join(HERE, "_build_bc" if bounds_check else "_build")
     os.makedirs(objdir, exist_ok=True)
-    objs = []
+    objs, cmds = [], []
     for src in sources():
         obj = os.path.join(objdir, os.path.basename(src) + ".o")
         cmd = [nvcc, *NVCC_FLAGS, "-I", INCLUDE, "-dc", src, "-o", obj]
@@ -49,8 +49,13 @@ def build(force=False, verbose=False, bounds_check=False):
             cmd.insert(1, "-DSNAP_BOUNDS_CHECK")
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
-        subprocess.check_call(cmd)
+        cmds.append(cmd)
         objs.append(obj)
+    # one nvcc process per source, as many at a time as there are cores
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
+            f.result()
     tmp = lib + ".tmp"
     subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", *objs,
                            "-o", tmp, "-lcudart"])

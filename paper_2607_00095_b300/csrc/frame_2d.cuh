@@ -54,6 +54,18 @@ __device__ __forceinline__ void frame_elems(const double *__restrict__ src, Fn &
   }
 }
 
+// x times an integer factor s of the grid (1 / (2 dx) = M, 1 / (4 dx^2) = M^2) in double-float:
+// scaling both parts is exact when M is a power of two; otherwise the exact product
+// (TwoProd of the leading part plus the scaled trailing part)
+template <int M>
+__device__ __forceinline__ df64 mul_grid(df64 x, float s) {
+  if constexpr ((M & (M - 1)) == 0) {
+    return df_scale2(x, s);
+  } else {
+    return x * df64(s, 0.0f);
+  }
+}
+
 __device__ __forceinline__ float fabs_max(float a, float b) {
   const float x = fabsf(b);
   return (a < x || x != x) ? x : a;
@@ -489,11 +501,12 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
     v.Rf[fd_slot<M>(s)] = v.Bh[s];
   }
   __syncthreads();
-  // scale = 4 dx^2 and its inverse are powers of two (N is)
-  const float scale_f = scale.hi, inv_scale_f = 1.0f / scale.hi;
+  // scale = 4 dx^2 = 1 / M^2: the float solve's correction is scaled by its float image (the
+  // next round's residual absorbs that rounding), the exact stencil residual by M^2
+  const float scale_f = scale.hi, inv_scale_f = (float)(M * M);
   for (int round = 0; round < REFINE; ++round) {
     if constexpr (M == 32) fd_solve_mma32(v.Rf, v.Tf, v.Q, v.Qt, v.I);
-    else if constexpr (M >= 8) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
+    else if constexpr (M >= 8 && M % 8 == 0) fd_solve_tiled<M>(v.Rf, v.Tf, v.Q, v.Qt, v.I);
     else fd_solve<M>(v.Rf, v.Tf, v.Q, v.I);
     for (int s = threadIdx.x; s < NN; s += T2D) {
       const df64 zz = df_add_fast(v.z(s), df64(v.Rf[fd_slot<M>(s)] * scale_f, 0.0f));
@@ -510,7 +523,7 @@ __device__ void poisson_frame(View2D<M> &v, const df64 &scale) {
                                                  v.z(base + q * M + (p + M - 1) % M)),
                                      df_add_fast(v.z(base + ((q + 1) % M) * M + p),
                                                  v.z(base + ((q + M - 1) % M) * M + p)));
-        const df64 az = df_scale2(df_sub_fast(df_scale2(zc, 4.0f), nb), inv_scale_f);
+        const df64 az = mul_grid<M>(df_sub_fast(df_scale2(zc, 4.0f), nb), inv_scale_f);
         const df64 r = df_sub_fast(df64(v.Bh[s], v.Bl[s]), az);
         v.Rf[fd_slot<M>(s)] = r.hi + r.lo;
       }
@@ -568,8 +581,8 @@ __device__ __forceinline__ df64 div_at_pairs(const float2 *xp, int i, int j, con
   constexpr int N = 2 * M, NN = N * N;
   const float2 ue = xp[j * N + (i + 1) % N], uw = xp[j * N + (i + N - 1) % N];
   const float2 vn = xp[NN + ((j + 1) % N) * N + i], vs = xp[NN + ((j + N - 1) % N) * N + i];
-  return df_scale2(df_add_fast(df_sub_fast(df64(ue.x, ue.y), df64(uw.x, uw.y)),
-                               df_sub_fast(df64(vn.x, vn.y), df64(vs.x, vs.y))), h2.hi);
+  return mul_grid<M>(df_add_fast(df_sub_fast(df64(ue.x, ue.y), df64(uw.x, uw.y)),
+                                 df_sub_fast(df64(vn.x, vn.y), df64(vs.x, vs.y))), h2.hi);
 }
 
 // (D w)(i, j) of a field held as doubles in shared memory, component 0 in w0, 1 in w1
@@ -581,7 +594,7 @@ __device__ __forceinline__ df64 div_at_smem(const double *w0, const double *w1, 
   const df64 uw = isplit(w0[j * N + (i + N - 1) % N]);
   const df64 vn = isplit(w1[((j + 1) % N) * N + i]);
   const df64 vs = isplit(w1[((j + N - 1) % N) * N + i]);
-  return df_scale2(df_add_fast(df_sub_fast(ue, uw), df_sub_fast(vn, vs)), h2.hi);
+  return mul_grid<M>(df_add_fast(df_sub_fast(ue, uw), df_sub_fast(vn, vs)), h2.hi);
 }
 
 // (D^T z) for element e of w[2][N][N] (component e / N^2)
@@ -589,8 +602,8 @@ template <int M>
 __device__ __forceinline__ df64 divT_at(const View2D<M> &v, int e, const df64 &h2) {
   constexpr int N = 2 * M, NN = N * N;
   const int comp = e / NN, cell = e % NN, i = cell % N, j = cell / N;
-  if (comp == 0) return df_scale2(df_sub_fast(v.z(cell_slot<M>(i - 1, j)), v.z(cell_slot<M>(i + 1, j))), h2.hi);
-  return df_scale2(df_sub_fast(v.z(cell_slot<M>(i, j - 1)), v.z(cell_slot<M>(i, j + 1))), h2.hi);
+  if (comp == 0) return mul_grid<M>(df_sub_fast(v.z(cell_slot<M>(i - 1, j)), v.z(cell_slot<M>(i + 1, j))), h2.hi);
+  return mul_grid<M>(df_sub_fast(v.z(cell_slot<M>(i, j - 1)), v.z(cell_slot<M>(i, j + 1))), h2.hi);
 }
 
 // Forward projection of frame f of one sample by the whole block (T2D threads, every thread

@@ -300,7 +300,30 @@ cudaError_t bwd_m(const snap_problem *p, int B, const double *gw, const double *
 
 }  // namespace
 
-bool supported_2d(int N) { return N == 4 || N == 8 || N == 16 || N == 32 || N == 64; }
+// every even side 4..64: the class size M = N / 2 is a template parameter of the frame code
+bool supported_2d(int N) { return N >= 4 && N <= 64 && N % 2 == 0; }
+
+// FN<M>(args...) for the class size M = N / 2 of a supported side N
+#define SNAP_DISPATCH_2D(N, FN, ...)                                                          \
+  switch ((N) / 2) {                                                                         \
+    case 2: e = FN<2>(__VA_ARGS__); break;   case 3: e = FN<3>(__VA_ARGS__); break;          \
+    case 4: e = FN<4>(__VA_ARGS__); break;   case 5: e = FN<5>(__VA_ARGS__); break;          \
+    case 6: e = FN<6>(__VA_ARGS__); break;   case 7: e = FN<7>(__VA_ARGS__); break;          \
+    case 8: e = FN<8>(__VA_ARGS__); break;   case 9: e = FN<9>(__VA_ARGS__); break;          \
+    case 10: e = FN<10>(__VA_ARGS__); break; case 11: e = FN<11>(__VA_ARGS__); break;        \
+    case 12: e = FN<12>(__VA_ARGS__); break; case 13: e = FN<13>(__VA_ARGS__); break;        \
+    case 14: e = FN<14>(__VA_ARGS__); break; case 15: e = FN<15>(__VA_ARGS__); break;        \
+    case 16: e = FN<16>(__VA_ARGS__); break; case 17: e = FN<17>(__VA_ARGS__); break;        \
+    case 18: e = FN<18>(__VA_ARGS__); break; case 19: e = FN<19>(__VA_ARGS__); break;        \
+    case 20: e = FN<20>(__VA_ARGS__); break; case 21: e = FN<21>(__VA_ARGS__); break;        \
+    case 22: e = FN<22>(__VA_ARGS__); break; case 23: e = FN<23>(__VA_ARGS__); break;        \
+    case 24: e = FN<24>(__VA_ARGS__); break; case 25: e = FN<25>(__VA_ARGS__); break;        \
+    case 26: e = FN<26>(__VA_ARGS__); break; case 27: e = FN<27>(__VA_ARGS__); break;        \
+    case 28: e = FN<28>(__VA_ARGS__); break; case 29: e = FN<29>(__VA_ARGS__); break;        \
+    case 30: e = FN<30>(__VA_ARGS__); break; case 31: e = FN<31>(__VA_ARGS__); break;        \
+    case 32: e = FN<32>(__VA_ARGS__); break;                                                  \
+    default: return cudaErrorNotSupported;                                                   \
+  }
 
 size_t ws_bytes_2d(const snap_problem *p, int B) {
   const size_t nfr = (size_t)B * p->desc.nt;
@@ -323,14 +346,7 @@ cudaError_t launch_2d_forward(const snap_problem *p, int B, const double *w_hat,
   const int N = p->desc.nx;
   cudaError_t e;
   const int pid = snap_prof_begin(s, "k2d_frame");
-  switch (N) {
-    case 4: e = fwd_m<2>(p, B, w_hat, params, w, lambda, wk.bst, o, s); break;
-    case 8: e = fwd_m<4>(p, B, w_hat, params, w, lambda, wk.bst, o, s); break;
-    case 16: e = fwd_m<8>(p, B, w_hat, params, w, lambda, wk.bst, o, s); break;
-    case 32: e = fwd_m<16>(p, B, w_hat, params, w, lambda, wk.bst, o, s); break;
-    case 64: e = fwd_m<32>(p, B, w_hat, params, w, lambda, wk.bst, o, s); break;
-    default: return cudaErrorNotSupported;
-  }
+  SNAP_DISPATCH_2D(N, fwd_m, p, B, w_hat, params, w, lambda, wk.bst, o, s);
   snap_prof_end(s, pid);
   if (e != cudaSuccess) return e;
   int launches = 1;
@@ -352,14 +368,7 @@ cudaError_t launch_2d_backward(const snap_problem *p, int B, const double *grad_
   const int N = p->desc.nx;
   cudaError_t e;
   const int pid = snap_prof_begin(s, "k2d_frame_bwd");
-  switch (N) {
-    case 4: e = bwd_m<2>(p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s); break;
-    case 8: e = bwd_m<4>(p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s); break;
-    case 16: e = bwd_m<8>(p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s); break;
-    case 32: e = bwd_m<16>(p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s); break;
-    case 64: e = bwd_m<32>(p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s); break;
-    default: return cudaErrorNotSupported;
-  }
+  SNAP_DISPATCH_2D(N, bwd_m, p, B, grad_w, w, lambda, params, stats, grad_w_hat, wk.contrib, s);
   snap_prof_end(s, pid);
   if (e != cudaSuccess) return e;
   int launches = 1;

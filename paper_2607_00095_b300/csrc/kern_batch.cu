@@ -814,6 +814,13 @@ SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *pro
     }
     b->n_blocks += (long long)G.n_inst * G.nt;
     if (p->desc.family == SNAP_FAMILY_C_DIV_ENERGY) {
+      // the batch kernel holds the frame code for the power-of-two sides only
+      const int side = p->desc.nx;
+      if (side != 4 && side != 8 && side != 16 && side != 32 && side != 64) {
+        delete b;
+        return snap_fail_msg(SNAP_ERR_UNSUPPORTED,
+                             "uneven batches take 2-D grid sides 4, 8, 16, 32 and 64 only");
+      }
       G.kind = 1;
       G.M = p->desc.nx / 2;
       if (ensure_2d_factor(p) != cudaSuccess) {

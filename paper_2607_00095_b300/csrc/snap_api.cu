@@ -382,7 +382,7 @@ snap_status snap_problem_create(const snap_problem_desc *d, snap_problem_t *out)
       }
       if (!supported_2d(d->nx)) {
         free(p);
-        return fail(SNAP_ERR_UNSUPPORTED, "2-D grid side must be 4, 8, 16, 32 or 64 in this build");
+        return fail(SNAP_ERR_UNSUPPORTED, "2-D grid side must be even and at most 64 in this build");
       }
       const int N = d->nx;
       p->info.n_vars = 2 * N * N * d->nt;

@@ -60,7 +60,7 @@ def test_pattern_1d_matches_oracle(family, nx, nt):
     assert p.n_rows_active == int(S.active.sum())
 
 
-@pytest.mark.parametrize("N,nt", [(4, 2), (8, 3), (64, 2)])
+@pytest.mark.parametrize("N,nt", [(4, 2), (8, 3), (64, 2), (6, 2), (12, 3)])
 def test_pattern_2d_matches_oracle(N, nt):
     p = Problem("C", N, nt)
     S = problems.structure_2d(N, nt)
@@ -198,3 +198,13 @@ def test_binding_rejects_short_buffers_without_launching():
         kw.update(bad)
         with pytest.raises(ValueError):
             p._check_sizes(B, **kw)
+
+
+def test_batch_rejects_2d_sides_it_does_not_hold_without_a_device():
+    """The uneven batch holds the frame code of the power-of-two sides only: a family C
+    problem of another side is refused when the batch is created (before any device work)."""
+    from paper_2607_00095_b300.api import Batch
+    with pytest.raises(_abi.SnapError) as ei:
+        Batch([Problem("C", 12, 2)], [0])
+    assert ei.value.code == 2
+    assert b"4, 8, 16, 32 and 64" in _abi.lib().snap_last_error()

@@ -17,7 +17,8 @@ def _gpu(N, nt, wh, pr, **kw):
     return p, u, lam, st, d
 
 
-@pytest.mark.parametrize("N,nt,B,seed", [(8, 3, 2, 301), (16, 2, 2, 302), (4, 2, 1, 303)])
+@pytest.mark.parametrize("N,nt,B,seed", [(8, 3, 2, 301), (16, 2, 2, 302), (4, 2, 1, 303),
+                                          (6, 3, 2, 305), (10, 2, 1, 306), (12, 2, 2, 307)])
 def test_2d_parity_dense_oracle(N, nt, B, seed):
     wh, pr = synthetic.gen_2d(seed, B, N, nt, kmax=max(1, min(8, N // 2 - 1)))
     p, u, lam, st, d = _gpu(N, nt, wh, pr)
@@ -31,9 +32,13 @@ def test_2d_parity_dense_oracle(N, nt, B, seed):
     assert st["h_inf"].max() <= H.H_TOL and st["kkt_inf"].max() <= 1e-10
 
 
-@pytest.mark.parametrize("N,nt,B,seed", [(64, 16, 64, 1003), (32, 8, 16, 304)])
+@pytest.mark.parametrize("N,nt,B,seed", [(64, 16, 64, 1003), (32, 8, 16, 304), (20, 3, 5, 308),
+                                          (24, 4, 8, 309), (48, 3, 6, 310), (62, 2, 3, 311),
+                                          (30, 2, 3, 312)])
 def test_2d_full_size_against_closed_form(N, nt, B, seed):
-    """The 2-D velocity workload (B=64, 64x64, 16 frames) and the uneven mix's 2-D size."""
+    """The 2-D velocity workload (B=64, 64x64, 16 frames), the uneven mix's 2-D size, and
+    sides that are not powers of two: class sizes M = N / 2 of 10 and 12 (the plain class
+    products), 24 (the register-tiled products), 31 and 15 (odd)."""
     wh, pr = synthetic.gen_2d(seed, B, N, nt)
     p, u, lam, st, d = _gpu(N, nt, wh, pr)
     np.testing.assert_array_equal(st["status"], 0)
@@ -48,8 +53,9 @@ def test_2d_full_size_against_closed_form(N, nt, B, seed):
     np.testing.assert_allclose(h.cpu().numpy()[:2], he, atol=1e-11)
 
 
-def test_2d_adjoint_against_oracle_and_fd():
-    N, nt, B = 8, 3, 2
+@pytest.mark.parametrize("N", [8, 12])
+def test_2d_adjoint_against_oracle_and_fd(N):
+    nt, B = 3, 2
     wh, pr = synthetic.gen_2d(311, B, N, nt, kmax=3)
     gbar = synthetic.gen_gbar(312, (B, nt * 2 * N * N))
     p, u, lam, st, d = _gpu(N, nt, wh, pr, tol_kkt=1e-13)
@@ -97,7 +103,9 @@ def test_2d_edge_cases():
     assert st["status"][1] == 3
     np.testing.assert_allclose(u[2], wc.reshape(1, -1)[0], rtol=0, atol=1e-12 * np.abs(wc).max())
     with pytest.raises(_abi.SnapError):
-        Problem("C", 12, 2)                     # grid sides outside {4, 8, 16, 32, 64}
+        Problem("C", 66, 2)                     # grid sides above 64
+    with pytest.raises(_abi.SnapError):
+        Problem("C", 7, 2)                      # odd grid side
     with pytest.raises(_abi.SnapError) as ei:
         p.project(d["uh"], d["pr"], u0=d["uh"] + 0.0)
     assert ei.value.code == 2

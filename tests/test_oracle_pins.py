@@ -300,7 +300,7 @@ def test_batch_permutation_exact():
 # 2-D: dense Newton-KKT against the FFT closed form
 # ---------------------------------------------------------------------------------------
 
-@pytest.mark.parametrize("N", [8, 16])
+@pytest.mark.parametrize("N", [6, 8, 12, 16])
 def test_2d_dense_newton_matches_fft_closed_form(N):
     nt, B = 2, 2
     wh, pr = synthetic.gen_2d(71 + N, B, N, nt, kmax=min(8, N // 2 - 1))
@@ -390,7 +390,7 @@ def test_adjoint_family_a_against_closed_form_fd():
     assert abs(fd - np.sum(a * d.reshape(a.shape))) <= 1e-5 * max(1.0, abs(fd))
 
 
-@pytest.mark.parametrize("N", [8, 16])
+@pytest.mark.parametrize("N", [6, 8, 16])
 def test_adjoint_2d_grad_params_against_closed_form_fd(N):
     """dL/d(K0, r2) of the 2-D family: the oracle's dense adjoint at its own solution, mapped
     through grad_params_2d, against central differences of the FFT closed form (a different
