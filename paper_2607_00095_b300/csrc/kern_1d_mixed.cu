@@ -54,7 +54,8 @@ __device__ __forceinline__ df64 shfl_df(df64 v, int off) {
 __global__ void __launch_bounds__(64, 8)
 k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
           const SampleDerived *__restrict__ sd, double *__restrict__ u,
-          double *__restrict__ lam, BlockStat *__restrict__ bst, SolverOpts o) {
+          double *__restrict__ lam, BlockStat *__restrict__ bst, SolverOpts o,
+          SliceOptsT<float> so_f, SliceOptsT<df64> so_d, df64 dxd) {
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2;        // group: slice 8*rho + q of round rho
   const int r = lane & 3;         // lane within the group
@@ -62,9 +63,9 @@ k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restri
   const long long ntiles = (total + 31) >> 5;
   const int wpb = blockDim.x >> 5;
   const int nx = g.nx, ih = g.ih;
-  const SliceOptsT<float> so_f = slice_opts<float>(o, o.tol_kkt);
-  const SliceOptsT<df64> so_d = slice_opts<df64>(o, o.tol_kkt);
-  const df64 dxd(g.dx);
+  // so_f, so_d, dxd: the options and dx in float and double-float, converted once on the host
+  // (the same conversion functions): each FP64 conversion here would hold the SM's narrow
+  // FP64 pipe for every thread of the launch before the first loads
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb) {
@@ -229,5 +230,9 @@ void launch_1d_mixed(const Geom1D &g, int B, const double *u_hat, const double *
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cudaLaunchKernelEx(&cfg, k1d_mixed, g, B, u_hat, params, sd, u, lambda, bst, o);
+  const SliceOptsT<float> so_f = slice_opts<float>(o, o.tol_kkt);
+  const SliceOptsT<df64> so_d = slice_opts<df64>(o, o.tol_kkt);
+  const df64 dxd(g.dx);
+  cudaLaunchKernelEx(&cfg, k1d_mixed, g, B, u_hat, params, sd, u, lambda, bst, o, so_f, so_d,
+                     dxd);
 }

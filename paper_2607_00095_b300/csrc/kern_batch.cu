@@ -53,6 +53,7 @@ struct GroupRec {
   int kind;                 // 0: 1-D, 1: 2-D
   int n_inst, list_off, nt, M;
   int lps;                  // 1-D: lanes per slice in the load / write-back passes (2, 4, 8)
+  df64 dxd;                 // 1-D: dx in double-float (converted on the host)
 };
 
 struct Item1D { int group, s0, s1; };     // slices [s0, s1) of the group's virtual batch
@@ -76,6 +77,10 @@ struct BatchArgs {
   BlockStat *bst;
   unsigned long long *t_ns;
   SolverOpts o;
+  // the options in float and double-float, converted once on the host (the same conversion
+  // functions as on the device): conversions here would load the narrow FP64 pipe per tile
+  SliceOptsT<float> so_f;
+  SliceOptsT<df64> so_d;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -248,9 +253,7 @@ __device__ __forceinline__ void run_subtile_1d(const BatchArgs &a, const GroupRe
   ad.sdw = sdw;
   ad.c = cx;
   ad.tol_kkt = a.o.tol_kkt;
-  const SliceOptsT<float> so_f = slice_opts<float>(a.o, a.o.tol_kkt);
-  const SliceOptsT<df64> so_d = slice_opts<df64>(a.o, a.o.tol_kkt);
-  mixed_tile(cx->g, ad, t0, t1, a.o, so_f, so_d, df64(cx->g.dx),
+  mixed_tile(cx->g, ad, t0, t1, a.o, a.so_f, a.so_d, G.dxd,
              G.lps == 2 ? 1 : (G.lps == 8 ? 3 : 2));
   __syncwarp();                          // the context is rewritten by the next tile
 }
@@ -714,6 +717,8 @@ snap_status launch_batch(snap_batch *b, const snap_options &o, unsigned long lon
   a.bst = (BlockStat *)(c + hdr_bytes(b));
   a.t_ns = t_ns;
   a.o = solver_opts(o);
+  a.so_f = slice_opts<float>(a.o, a.o.tol_kkt);
+  a.so_d = slice_opts<df64>(a.o, a.o.tol_kkt);
   cudaError_t e = cudaMemsetAsync(ws, 0, hdr_bytes(b), s);
   if (e != cudaSuccess) return snap_fail_msg(SNAP_ERR_CUDA, cudaGetErrorString(e));
   k_batch<<<b->grid, kThreads, b->smem_bytes, s>>>(a);
@@ -834,6 +839,7 @@ SNAP_API snap_status snap_batch_create(int n_problems, const snap_problem_t *pro
     } else {
       G.kind = 0;
       G.g = p->g1;
+      G.dxd = df64(p->g1.dx);
       // the smallest item size (16 slices) gives the most items
       cap1_packed += ((size_t)G.n_inst * G.nt + 15) / 16;
       cap1_split += (size_t)G.n_inst * ((G.nt + 15) / 16);
