@@ -4,6 +4,8 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libsnap.so")
+# the diagnostic build (-DSNAP_BOUNDS_CHECK), loaded instead when SNAP_BOUNDS_CHECK=1
+LIB_BC_PATH = os.path.join(HERE, "libsnap_bc.so")
 
 SNAP_OK = 0
 NOALLOC_SCRATCH_BYTES = 8388608
@@ -111,13 +113,15 @@ class SnapError(RuntimeError):
 
 
 def lib():
-    """Load libsnap.so; raises if the extension has not been built (no fallback)."""
+    """Load libsnap.so (libsnap_bc.so, the bounds-checked build, when the environment sets
+    SNAP_BOUNDS_CHECK=1); raises if that library has not been built (no fallback)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise ImportError(f"libsnap.so not built ({LIB_PATH}); run "
+        path = LIB_BC_PATH if os.environ.get("SNAP_BOUNDS_CHECK") == "1" else LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"{os.path.basename(path)} not built ({path}); run "
                               "python -m paper_2607_00095_b300.build or __graft_entry__.build()")
-        L = C.CDLL(LIB_PATH)
+        L = C.CDLL(path)
         for name, (res, args) in _PROTOS.items():
             f = getattr(L, name)
             f.restype = res
