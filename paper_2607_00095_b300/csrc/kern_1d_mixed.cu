@@ -30,9 +30,10 @@
 // [2^-74, 2^57], exactly zero, or non-finite) falls back to FP64 moments and the FP64
 // iteration.
 //
-// Phase 2 is t1_solve_slice (tile_1d.cuh), the same device code as the uneven-batch kernel's
-// tile; phases 1 and 3 stay inline here (the batch kernel locates its slices through a
-// per-instance pointer table instead).
+// The three phases are the warp tile mixed_tile (tile_1d.cuh), the device code of the
+// uneven-batch kernel too, instantiated here with 4 lanes per slice and 16 loads in flight per
+// lane and an address policy over the rows of one batch (the batch kernel locates its slices
+// through a per-instance pointer table instead).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -43,171 +44,66 @@
 
 namespace {
 
-constexpr unsigned FULL = 0xffffffffu;
+// Slices of the per-problem batch: slice s = b nt + k is row s of u_hat / u, its sample's
+// parameters, multipliers and derived values are at b.
+struct DirectTiles {
+  const double *uh, *params;
+  const SampleDerived *sd;
+  double *u, *lam;
+  BlockStat *bst;
+  long long total;
+  int nt, nx, n_params, n_rows;
+  __device__ __forceinline__ int slice_k(long long s) const { return (int)(s % nt); }
+  __device__ __forceinline__ long long sample(long long s) const { return s / nt; }
+  __device__ __forceinline__ const double *row_in(long long s) const { return uh + (size_t)s * nx; }
+  __device__ __forceinline__ double *row_out(long long s) const { return u + (size_t)s * nx; }
+  __device__ __forceinline__ const double *par(long long s) const {
+    return params + (size_t)sample(s) * n_params;
+  }
+  __device__ __forceinline__ double *lam_of(long long s) const {
+    return lam + (size_t)sample(s) * n_rows;
+  }
+  __device__ __forceinline__ SampleDerived derived(long long s) const { return sd[sample(s)]; }
+  __device__ __forceinline__ BlockStat *stat(long long s) const { return bst + s; }
+  // pull the tile (consecutive slices, contiguous in HBM) into L2 ahead of the loads
+  __device__ __forceinline__ void prefetch(long long s0, long long s1, int lane) const {
+    const char *t0 = reinterpret_cast<const char *>(uh + (size_t)s0 * nx);
+    const size_t bytes = (size_t)(s1 - s0) * nx * sizeof(double);
+    for (size_t off = (size_t)lane * 128; off < bytes; off += 32 * 128)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(t0 + off));
+  }
+  // the per-sample values come from k1d_params (programmatic dependency)
+  __device__ __forceinline__ void before_solve(long long, long long, int) const {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+  }
+  __device__ __forceinline__ bool row_ok(int site, long long s, int i) const {
+    return snap_in_bounds(site, s * nx + i + 1, total * nx);
+  }
+  __device__ __forceinline__ bool slice_ok(long long s) const {
+    return snap_in_bounds(SNAP_SITE_MIXED_ROW, s, total);
+  }
+};
 
-enum { KIND_MOMENT = 0, KIND_NONE = 3 };
-
-__device__ __forceinline__ df64 shfl_df(df64 v, int off) {
-  return df64(__shfl_xor_sync(FULL, v.hi, off), __shfl_xor_sync(FULL, v.lo, off));
-}
-
+// One warp per tile of 32 consecutive slices (the shared warp tile mixed_tile of tile_1d.cuh
+// with 4 lanes per slice and 16 loads in flight per lane); a grid-stride loop over the tiles.
 __global__ void __launch_bounds__(64, 8)
 k1d_mixed(Geom1D g, int B, const double *__restrict__ uh, const double *__restrict__ params,
           const SampleDerived *__restrict__ sd, double *__restrict__ u,
           double *__restrict__ lam, BlockStat *__restrict__ bst, SolverOpts o,
           SliceOptsT<float> so_f, SliceOptsT<df64> so_d, df64 dxd) {
-  const int lane = threadIdx.x & 31;
-  const int q = lane >> 2;        // group: slice 8*rho + q of round rho
-  const int r = lane & 3;         // lane within the group
-  const long long total = (long long)B * g.nt;
-  const long long ntiles = (total + 31) >> 5;
-  const int wpb = blockDim.x >> 5;
-  const int nx = g.nx, ih = g.ih;
   // so_f, so_d, dxd: the options and dx in float and double-float, converted once on the host
   // (the same conversion functions): each FP64 conversion here would hold the SM's narrow
   // FP64 pipe for every thread of the launch before the first loads
+  const long long total = (long long)B * g.nt;
+  const long long ntiles = (total + 31) >> 5;
+  const int wpb = blockDim.x >> 5;
+  const DirectTiles ad{uh, params, sd, u, lam, bst, total, g.nt, g.nx, g.n_params, g.n_rows};
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb) {
     const long long sbase = tile << 5;
-    // ---------------- phase 1 ----------------
-    {
-      // pull the tile (32 consecutive slices, contiguous in HBM) into L2 ahead of the loads
-      const long long s_end = (sbase + 32 < total) ? sbase + 32 : total;
-      const char *t0 = reinterpret_cast<const char *>(uh + (size_t)sbase * nx);
-      const size_t bytes = (size_t)(s_end - sbase) * nx * sizeof(double);
-      for (size_t off = (size_t)lane * 128; off < bytes; off += 32 * 128)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(t0 + off));
-    }
-    df64 m1(0.0f, 0.0f), m2(0.0f, 0.0f);
-    float mmx = -INFINITY, mmn = INFINITY;
-    int mok = 1;
-#pragma unroll 1
-    for (int rho = 0; rho < 4; ++rho) {
-      const long long s = sbase + 8 * rho + q;
-      float s1h = 0.0f, s1e = 0.0f, s2h = 0.0f, s2e = 0.0f;
-      float pmx = -INFINITY, pmn = INFINITY;
-      int ok = 1;
-      if (s < total) {
-        const int k = (int)(s % g.nt);
-        const double *row = uh + (size_t)s * nx;
-        if (k == 0) {
-          // the IC slice is handled by the per-sample prepare kernel
-        } else {
-          // CH independent 16-byte loads in flight per lane, then the accumulation
-          constexpr int CH = 16;
-          for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
-            double2 v[CH];
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-              const int i = i0 + 8 * c;
-              v[c] = (i < nx && snap_in_bounds(SNAP_SITE_MOMENT_ROW, s * nx + i + 1, total * nx))
-                         ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
-            }
-#pragma unroll
-            for (int c = 0; c < CH; ++c) {
-              const int i = i0 + 8 * c;
-              if (i >= nx) break;
-              float h0, l0, h1, l1;
-              ok &= df_split_trunc_fast(v[c].x, h0, l0);
-              ok &= df_split_trunc_fast(v[c].y, h1, l1);
-              if (i == 0 || i == ih) { h0 = 0.0f; l0 = 0.0f; }
-              if (i + 1 == ih) { h1 = 0.0f; l1 = 0.0f; }
-              else { pmx = fmaxf(pmx, h1); pmn = fminf(pmn, h1); }
-              if (i != 0 && i != ih) { pmx = fmaxf(pmx, h0); pmn = fminf(pmn, h0); }
-              // S1 += h + l (TwoSum on the leading parts, errors accumulated in s1e)
-              {
-                float t = s1h + h0, bb = t - s1h;
-                s1e += ((s1h - (t - bb)) + (h0 - bb)) + l0;
-                s1h = t;
-                t = s1h + h1; bb = t - s1h;
-                s1e += ((s1h - (t - bb)) + (h1 - bb)) + l1;
-                s1h = t;
-              }
-              // S2 += (h + l)^2 = h^2 (TwoProd) + 2 h l (+ l^2, below 2^-48 relative)
-              {
-                float p = h0 * h0;
-                float pe = fmaf(h0, h0, -p);
-                pe = fmaf(h0 + h0, l0, pe);
-                float t = s2h + p, bb = t - s2h;
-                s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
-                s2h = t;
-                p = h1 * h1;
-                pe = fmaf(h1, h1, -p);
-                pe = fmaf(h1 + h1, l1, pe);
-                t = s2h + p; bb = t - s2h;
-                s2e += ((s2h - (t - bb)) + (p - bb)) + pe;
-                s2h = t;
-              }
-            }
-          }
-        }
-      }
-      df64 a1 = df_fast_two_sum(s1h, s1e);
-      df64 a2 = df_fast_two_sum(s2h, s2e);
-#pragma unroll
-      for (int off = 1; off < 4; off <<= 1) {
-        a1 = a1 + shfl_df(a1, off);
-        a2 = a2 + shfl_df(a2, off);
-        pmx = fmaxf(pmx, __shfl_xor_sync(FULL, pmx, off));
-        pmn = fminf(pmn, __shfl_xor_sync(FULL, pmn, off));
-        ok &= __shfl_xor_sync(FULL, ok, off);
-      }
-      if (r == rho) {
-        m1 = a1; m2 = a2; mmx = pmx; mmn = pmn; mok = ok;
-      }
-    }
-    // ---------------- phase 2: one slice per lane ----------------
-    // the per-sample values come from k1d_params (programmatic dependency)
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const long long s = sbase + 8 * r + q;
-    int kind = KIND_NONE;
-    double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
-    if (s < total && (s % g.nt) != 0 && snap_in_bounds(SNAP_SITE_MIXED_ROW, s, total)) {
-      // the IC slice (k = 0) is written by the prepare kernel
-      const int b = (int)(s / g.nt);
-      const int k = (int)(s % g.nt);
-      const double *row = uh + (size_t)s * nx;
-      kind = KIND_MOMENT;
-      t1_solve_slice(g, k, m1, m2, mmx, mmn, mok, __ldg(row), __ldg(row + ih), row,
-                     params + (size_t)b * g.n_params, sd[b], lam + (size_t)b * g.n_rows, bst + s,
-                     o, so_f, so_d, dxd, A, Cc, P0, PH);
-    }
-    // ---------------- phase 3: write-back, 4 lanes per slice ----------------
-#pragma unroll 1
-    for (int rho = 0; rho < 4; ++rho) {
-      const int src = 4 * q + rho;
-      const double a = __shfl_sync(FULL, A, src);
-      const double c0 = __shfl_sync(FULL, Cc, src);
-      const double p0 = __shfl_sync(FULL, P0, src);
-      const double ph = __shfl_sync(FULL, PH, src);
-      const int kd = __shfl_sync(FULL, kind, src);
-      const long long s2 = sbase + 8 * rho + q;
-      if (s2 >= total || kd == KIND_NONE) continue;
-      const double *row = uh + (size_t)s2 * nx;
-      double *out = u + (size_t)s2 * nx;
-      if (kd == KIND_MOMENT) {
-        constexpr int CH = 16;
-        for (int i0 = 2 * r; i0 < nx; i0 += 8 * CH) {
-          double2 v[CH];
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
-            v[c] = (i < nx) ? *reinterpret_cast<const double2 *>(row + i) : make_double2(0.0, 0.0);
-          }
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int i = i0 + 8 * c;
-            if (i >= nx) break;
-            double2 w;
-            w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v[c].x, c0));
-            w.y = (i + 1 == ih) ? ph : fma(a, v[c].y, c0);
-            if (snap_in_bounds(SNAP_SITE_MIXED_ROW, s2 * nx + i + 1, total * nx))
-              *reinterpret_cast<double2 *>(out + i) = w;
-          }
-        }
-      }
-    }
+    const long long send = (sbase + 32 < total) ? sbase + 32 : total;
+    mixed_tile<DirectTiles, 2, 16>(g, ad, sbase, send, o, so_f, so_d, dxd, 2);
   }
 }
 

@@ -125,6 +125,10 @@ struct BatchTiles {
     return sdw[inst_of(s) - c->first_inst];
   }
   __device__ __forceinline__ BlockStat *stat(long long s) const { return c->bst + (int)s; }
+  // the bounds-checked build checks the per-problem kernels; the batch's slices are located
+  // through the instance table
+  __device__ __forceinline__ bool row_ok(int, long long, int) const { return true; }
+  __device__ __forceinline__ bool slice_ok(long long) const { return true; }
   __device__ __forceinline__ void prefetch(long long s0l, long long s1l, int lane) const {
     const int s0 = (int)s0l, s1 = (int)s1l, n = nt();
     for (int i = s0 / n; i * n < s1; ++i) {

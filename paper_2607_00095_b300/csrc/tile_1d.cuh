@@ -1,8 +1,8 @@
 // The warp tile of the 1-D mixed-pipe moment path (families A/B, start u0 = u_hat): one warp
 // projects up to 32 consecutive slices [sbase, send) of a virtual batch whose slices are
-// located by the address policy Addr.  Used by the uneven-batch kernel (kern_batch.cu, one
-// pointer set per instance); it is the tile of the per-problem kernel k1d_mixed
-// (kern_1d_mixed.cu), which keeps the same phases inline in its grid-stride loop for speed.
+// located by the address policy Addr.  The tile of the per-problem kernel k1d_mixed
+// (kern_1d_mixed.cu: rows of one batch, 4 lanes per slice, 16 loads in flight) and of the
+// uneven-batch kernel (kern_batch.cu: one pointer set per instance, lanes per slice per group).
 //
 //   phase 1  (LPS = 2, 4 or 8 lanes per slice, 32 / LPS slices per warp instruction, 16-byte
 //            loads): every u_hat_i is split into a float pair hi + lo with integer operations
@@ -27,7 +27,9 @@
 //   par(s) / lam_of(s)      the parameters / multipliers of its sample;
 //   derived(s)              the sample's SampleDerived;  stat(s)  its BlockStat slot;
 //   prefetch(s0, s1, lane)  L2 prefetch of the tile's u_hat;
-//   before_solve(s0, s1, lane)  hook run by the whole warp between phases 1 and 2.
+//   before_solve(s0, s1, lane)  hook run by the whole warp between phases 1 and 2;
+//   row_ok(site, s, i) / slice_ok(s)  the bounds-checked build's checks of the accesses to
+//                                      elements i, i + 1 of slice s / of slice s (true otherwise).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -35,6 +37,7 @@
 #include <stdint.h>
 
 #include "slice_newton.cuh"
+#include "snap_bounds.cuh"
 #include "snap_internal.h"
 
 namespace {
@@ -185,19 +188,22 @@ __device__ __forceinline__ void t1_solve_slice(
   *stat = st;
 }
 
-// LPS = 2^lps_log2 lanes per slice in phases 1 and 3 (2, 4 or 8; a runtime value, so that one
-// instance of the tile serves every group): 32 / LPS slices per round, LPS rounds.  A different
-// LPS sums the moments in a different order (results agree to rounding).
-template <class Addr>
+// LPS = 2^lg lanes per slice in phases 1 and 3 (2, 4 or 8): 32 / LPS slices per round, LPS
+// rounds.  LPS_LOG2 > 0 fixes lg at compile time (the per-problem kernel); LPS_LOG2 = 0 takes
+// lg = lps_log2 at run time, so that one instance of the tile serves every group of the uneven
+// batch.  A different LPS sums the moments in a different order (results agree to rounding).
+// CH: 16-byte loads in flight per lane in phases 1 and 3.
+template <class Addr, int LPS_LOG2 = 0, int CH = 8>
 __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long long sbase,
                                            long long send, const SolverOpts &o,
                                            const SliceOptsT<float> &so_f,
                                            const SliceOptsT<df64> &so_d, const df64 &dxd,
                                            int lps_log2) {
-  const int LPS = 1 << lps_log2;
-  const int SPR = 32 >> lps_log2;   // slices per round
+  const int lg = LPS_LOG2 > 0 ? LPS_LOG2 : lps_log2;
+  const int LPS = 1 << lg;
+  const int SPR = 32 >> lg;         // slices per round
   const int lane = threadIdx.x & 31;
-  const int q = lane >> lps_log2;   // group: slice SPR*rho + q of round rho
+  const int q = lane >> lg;         // group: slice SPR*rho + q of round rho
   const int r = lane & (LPS - 1);   // lane within the group
   const int nx = g.nx, ih = g.ih;
   // ---------------- phase 1 ----------------
@@ -218,13 +224,13 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
         // the IC slice is handled by the per-sample prepare kernel
       } else {
         // CH independent 16-byte loads in flight per lane, then the accumulation
-        constexpr int CH = 8;
         for (int i0 = 2 * r; i0 < nx; i0 += 2 * LPS * CH) {
           double2 v[CH];
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
             const int i = i0 + 2 * LPS * c;
-            v[c] = (i < nx) ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
+            v[c] = (i < nx && ad.row_ok(SNAP_SITE_MOMENT_ROW, s, i))
+                       ? __ldg(reinterpret_cast<const double2 *>(row + i)) : make_double2(0.0, 0.0);
           }
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
@@ -284,7 +290,7 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
   const long long s = sbase + SPR * r + q;
   int kind = T1_KIND_NONE;
   double A = 1.0, Cc = 0.0, P0 = 0.0, PH = 0.0;
-  if (s < send) {
+  if (s < send && ad.slice_ok(s)) {
     const int k = ad.slice_k(s);
     if (k != 0) {     // IC slice (k = 0): solved by the caller
       const double *row = ad.row_in(s);
@@ -308,7 +314,6 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
     const double *row = ad.row_in(s2);
     double *out = ad.row_out(s2);
     if (kd == T1_KIND_MOMENT) {
-      constexpr int CH = 8;
       for (int i0 = 2 * r; i0 < nx; i0 += 2 * LPS * CH) {
         double2 v[CH];
 #pragma unroll
@@ -323,7 +328,7 @@ __device__ __forceinline__ void mixed_tile(const Geom1D &g, const Addr &ad, long
           double2 w;
           w.x = (i == 0) ? p0 : ((i == ih) ? ph : fma(a, v[c].x, c0));
           w.y = (i + 1 == ih) ? ph : fma(a, v[c].y, c0);
-          *reinterpret_cast<double2 *>(out + i) = w;
+          if (ad.row_ok(SNAP_SITE_MIXED_ROW, s2, i)) *reinterpret_cast<double2 *>(out + i) = w;
         }
       }
     }
