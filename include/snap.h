@@ -285,8 +285,9 @@ SNAP_API snap_status snap_project(snap_problem_t p, int B, const double *u_hat, 
  *   u, lambda   forward outputs (device, read)
  *   params      forward parameters (device, read)
  *   stats       forward stats (device) or NULL; samples whose status is not OK get NaN
- *   grad_u_hat  [B][n_vars]    (device, written)
- *   grad_params [B][n_params]  (device, written) or NULL; layout of params
+ *   grad_u_hat  [B][n_vars]    (device, written; may not alias grad_u or u)
+ *   grad_params [B][n_params]  (device, written; may not alias params) or NULL; layout of
+ *                              params
  *   workspace   snap_workspace_size(p, B) bytes
  * Errors as snap_project. */
 SNAP_API snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,

@@ -560,6 +560,8 @@ snap_status snap_project_backward(snap_problem_t p, int B, const double *grad_u,
     return fail(SNAP_ERR_INVALID_ARG, "null grad_u / u / lambda / params / grad_u_hat");
   if (!aligned16(grad_u) || !aligned16(u) || !aligned16(grad_u_hat))
     return fail(SNAP_ERR_INVALID_ARG, "grad_u, u and grad_u_hat must be 16-byte aligned");
+  if (grad_u_hat == grad_u || grad_u_hat == u || (grad_params && grad_params == params))
+    return fail(SNAP_ERR_INVALID_ARG, "outputs may not alias inputs");
   const size_t need = ws_bytes(p, B);
   if (need > 0 && (!workspace || workspace_bytes < need))
     return fail(SNAP_ERR_WORKSPACE, "workspace of %zu bytes required (got %zu)", need, workspace_bytes);

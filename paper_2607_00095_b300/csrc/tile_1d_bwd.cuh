@@ -61,16 +61,12 @@ __device__ __forceinline__ void tb_acc_prod(float &s, float &e, float xh, float 
   s = t;
 }
 
-// L2 residency hints for the adjoint tile: u and dL/du are read twice (the sums of phase 1,
+// L2 residency hint for the adjoint tile: u and dL/du are read twice (the sums of phase 1,
 // the write-back of phase 3) and the whole batch's u and dL/du are in flight at once, so the
-// first reads keep their lines (evict_last), the second reads and the dL/du_hat stores mark
-// theirs for early eviction (evict_first): the outputs stream through L2 without pushing out
-// inputs that other tiles have still to re-read.
-__device__ __forceinline__ unsigned long long tb_policy_keep() {
-  unsigned long long p;
-  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
+// second reads and the dL/du_hat stores mark their lines for early eviction (evict_first): the
+// outputs stream through L2 without pushing out inputs that other tiles have still to re-read.
+// The second reads take the non-coherent path: the kernel never writes u or dL/du (the entry
+// point refuses outputs that alias them).
 __device__ __forceinline__ unsigned long long tb_policy_drop() {
   unsigned long long p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));

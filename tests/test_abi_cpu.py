@@ -118,6 +118,11 @@ def test_null_and_size_errors_without_gpu():
     bad = options(tol_kkt=-1.0)
     rc = L.snap_project(p.handle, 2, fake, fake, None, fake, fake, None, C.byref(bad), None, 0, None)
     assert rc == 1
+    # the adjoint refuses outputs that alias its inputs, before any launch
+    g1, g2 = C.c_void_p(4 << 20), C.c_void_p(5 << 20)
+    for gu, uu, gh in ((g1, g2, g1), (g1, g2, g2)):
+        rc = L.snap_project_backward(p.handle, 2, gu, uu, fake, fake, None, gh, None, None, 0, None)
+        assert rc == 1 and b"alias" in L.snap_last_error()
     t = Problem("toy", 3, 3)
     rc = L.snap_project(t.handle, 1, fake, fake, None, fake, fake, None, C.byref(o), None, 0, None)
     assert rc == 2
