@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(128, 4)
 k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__restrict__ u,
               const double *__restrict__ lam, const snap_stats *__restrict__ fst,
               const SampleDerived *__restrict__ sd, double *__restrict__ gh,
-              double *__restrict__ gp, BwdContrib *__restrict__ contrib) {
+              double *__restrict__ gp, BwdContrib *__restrict__ contrib, df64 dxd) {
   const long long total = (long long)B * g.nt;
   const long long ntiles = (total + 31) >> 5;
   const int wpb = blockDim.x >> 5;
@@ -57,7 +57,7 @@ k1d_bwd_mixed(Geom1D g, int B, const double *__restrict__ gu, const double *__re
                      contrib};
   for (long long tile = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); tile < ntiles;
        tile += (long long)gridDim.x * wpb)
-    bwd_tile(g, ad, tile << 5);
+    bwd_tile(g, ad, tile << 5, dxd);
 }
 
 }  // namespace
@@ -80,6 +80,7 @@ void launch_1d_bwd_mixed(const Geom1D &g, int B, const double *grad_u, const dou
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  const df64 dxd(g.dx);
   cudaLaunchKernelEx(&cfg, k1d_bwd_mixed, g, B, grad_u, u, lambda, stats, sd, grad_u_hat,
-                     grad_params, contrib);
+                     grad_params, contrib, dxd);
 }

@@ -493,7 +493,7 @@ __device__ __forceinline__ void batch_1d_bwd(const BwdArgs &a, SampleDerived *sd
       ad.c = cx;
       ad.s0 = t0;
       ad.s1 = t1;
-      bwd_tile(cx->g, ad, t0);
+      bwd_tile(cx->g, ad, t0, G.dxd);
       __syncwarp();
     }
     // arrival: every lane's contributions and outputs are fenced before lane 0 counts

@@ -234,13 +234,15 @@ __device__ __forceinline__ BwdCoef bwd_slice(const Geom1D &g, const Bwd &ad, lon
 }
 
 template <class Bwd>
-__device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long long sbase) {
+// dxd: dx in double-float, converted on the host (a conversion here would hold the FP64 pipe
+// ahead of the tile's first loads)
+__device__ __forceinline__ void bwd_tile(const Geom1D &g, const Bwd &ad, long long sbase,
+                                         const df64 &dxd) {
   constexpr unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int q = lane >> 2;
   const int r = lane & 3;
   const int nx = g.nx, ih = g.ih;
-  const df64 dxd(g.dx);
   const unsigned long long pol_drop = tb_policy_drop();
   // ---------------- phase 1: sums over the interior ----------------
   df64 mg(0.0f, 0.0f), mug(0.0f, 0.0f), mu(0.0f, 0.0f), muu(0.0f, 0.0f);
