@@ -34,6 +34,15 @@ __device__ __forceinline__ df64 isplit(double x) {
   return df_from_double_slow(x);         // out of the pair range: FP64 conversion
 }
 
+// dx = 1 / N and 4 dx^2 of the N = 2M grid in double-float, formed at compile time: a
+// conversion at run time is FP64-pipe work for every thread ahead of the frame's first loads
+template <int M>
+struct GridConst {
+  static constexpr double dx = 1.0 / (2 * M), sc = 4.0 / ((2.0 * M) * (2.0 * M));
+  static constexpr float dx_hi = (float)dx, dx_lo = (float)(dx - (double)dx_hi);
+  static constexpr float sc_hi = (float)sc, sc_lo = (float)(sc - (double)sc_hi);
+};
+
 // fn(e, x) for every element e of a frame's 2 N^2 doubles x = src[e] (thread-strided), with
 // FB loads in flight per thread before the first use (the passes are latency-bound otherwise)
 constexpr int FB = 8;
@@ -625,8 +634,8 @@ __device__ void frame2d_forward(View2D<M> &v, const double *__restrict__ src,
                                 BlockStat *__restrict__ out, const SolverOpts &o) {
   constexpr int N = 2 * M, NN = N * N;
   const df64 h2((float)N * 0.5f, 0.0f);          // 1 / (2 dx), exact
-  const df64 dx(1.0 / N);
-  const df64 scale = df64(4.0 / ((double)N * (double)N));   // 4 dx^2
+  const df64 dx(GridConst<M>::dx_hi, GridConst<M>::dx_lo);
+  const df64 scale(GridConst<M>::sc_hi, GridConst<M>::sc_lo);   // 4 dx^2
   load_class_factor<M>(v, Qg, Ig);
   // w_hat as float pairs in the Poisson work area (z hi / lo, r, t: 4 N^2 floats = 2 N^2 pairs)
   float2 *xp = reinterpret_cast<float2 *>(v.Zh);
@@ -765,8 +774,8 @@ __device__ void frame2d_backward(View2D<M> &v, const double *__restrict__ gsrc,
                                  double *__restrict__ dst, BwdContrib *__restrict__ contrib) {
   constexpr int N = 2 * M, NN = N * N;
   const df64 h2((float)N * 0.5f, 0.0f);
-  const df64 dx(1.0 / N);
-  const df64 scale = df64(4.0 / ((double)N * (double)N));
+  const df64 dx(GridConst<M>::dx_hi, GridConst<M>::dx_lo);
+  const df64 scale(GridConst<M>::sc_hi, GridConst<M>::sc_lo);   // 4 dx^2
   load_class_factor<M>(v, Qg, Ig);
   // gbar as float pairs in the Poisson work area for the divergence stencil (as the forward)
   float2 *gp2 = reinterpret_cast<float2 *>(v.Zh);
