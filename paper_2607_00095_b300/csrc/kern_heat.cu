@@ -164,6 +164,11 @@ __device__ __forceinline__ void heat_neighbours(const double (&v)[E], double (&l
 struct HeatArgs {
   int B, nx, nt, n_rows, off_mass, off_pde, off_energy;
   double dx, dt;
+  // grid constants formed on the host (FP64 divisions and conversions in the kernel would be
+  // FP64-pipe work for every thread ahead of the time chain): dt / (2 dx^2), 1 / dt, 1 / (4 dx),
+  // and dx, dx / 2, 1 / dt, dt, 1 / (2 dx^2) in double-float
+  double kfac, idt, ce_fac;
+  df64 dx_d, half_dx_d, idt_d, dt_d, cd2_d;
   const double *uh;       // forward: u_hat; adjoint: dL/du
   const double *params;   // [B][nx + 1] = g, alpha
   const double *u;        // adjoint / residual: the projection
@@ -416,16 +421,16 @@ struct HeatRowsDF {
   df64 dx, half_dx, idt, ce;   // dx, dx / 2, 1 / dt, alpha / (4 dx)
 };
 
-__device__ __forceinline__ HeatRowsDF heat_rows_df(double alpha, double dx, double dt) {
-  const double kap = alpha * dt / (2.0 * dx * dx);
+__device__ __forceinline__ HeatRowsDF heat_rows_df(double alpha, const HeatArgs &a) {
+  const double kap = alpha * a.kfac;
   HeatRowsDF r;
-  r.c1 = df64((1.0 + 2.0 * kap) / dt);
-  r.c2 = df64((1.0 - 2.0 * kap) / dt);
-  r.c3 = df64(kap / dt);
-  r.dx = df64(dx);
-  r.half_dx = df64(0.5 * dx);
-  r.idt = df64(1.0 / dt);
-  r.ce = df64(alpha / (4.0 * dx));
+  r.c1 = df64((1.0 + 2.0 * kap) * a.idt);
+  r.c2 = df64((1.0 - 2.0 * kap) * a.idt);
+  r.c3 = df64(kap * a.idt);
+  r.dx = a.dx_d;
+  r.half_dx = a.half_dx_d;
+  r.idt = a.idt_d;
+  r.ce = df64(alpha * a.ce_fac);
   return r;
 }
 
@@ -544,8 +549,8 @@ __device__ __forceinline__ bool heat_forward_df(const HeatArgs &a, int b, int la
   double *ub = a.u_out + (size_t)b * nx * nt;
   const double *uhb = a.uh + (size_t)b * nx * nt;
   double *lb = a.lam + (size_t)b * a.n_rows;
-  const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
-  const df64 dt_d = df64(a.dt);
+  const HeatRowsDF c = heat_rows_df(alpha, a);
+  const df64 dt_d = a.dt_d;
   HeatFactorDF<E> f;
   if (w == 0) heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
   // warp 1: row statistics and objective
@@ -757,9 +762,9 @@ __device__ __forceinline__ bool heat_backward_df(const HeatArgs &a, int b, int l
   double *gh = a.grad_uh + (size_t)b * nx * nt;
   double *gp = a.grad_params ? a.grad_params + (size_t)b * (nx + 1) : nullptr;
   const df64 zero(0.0f, 0.0f);
-  const HeatRowsDF c = heat_rows_df(alpha, a.dx, a.dt);
-  const df64 dt_d = df64(a.dt);
-  const df64 cd2 = df64(0.5 / (a.dx * a.dx));
+  const HeatRowsDF c = heat_rows_df(alpha, a);
+  const df64 dt_d = a.dt_d;
+  const df64 cd2 = a.cd2_d;
   HeatFactorDF<E> f;
   if (w == 0) heat_factor_df<E>(f, alpha, a.dx, a.dt, nx, lane);
   // warp 1 state: dt gbar of the next step and u^{k+1}, u^k, u^{k-1} around the pending term
@@ -1153,6 +1158,14 @@ HeatArgs heat_args(const snap_problem *p, int B) {
   a.off_energy = a.off_pde + (a.nt - 1) * a.nx;
   a.dx = 2.0 * 3.14159265358979323846 / a.nx;
   a.dt = 1.0 / (a.nt - 1);
+  a.kfac = a.dt / (2.0 * a.dx * a.dx);
+  a.idt = 1.0 / a.dt;
+  a.ce_fac = 1.0 / (4.0 * a.dx);
+  a.dx_d = df64(a.dx);
+  a.half_dx_d = df64(0.5 * a.dx);
+  a.idt_d = df64(a.idt);
+  a.dt_d = df64(a.dt);
+  a.cd2_d = df64(0.5 / (a.dx * a.dx));
   return a;
 }
 
